@@ -1,0 +1,183 @@
+/*
+ * lsm.h - C ABI of the GB300 matrix-free elastic Lippmann-Schwinger solver.
+ *
+ * The library solves the discretised Lippmann-Schwinger (LS) equation for
+ * the frequency-domain displacement u in a heterogeneous anisotropic elastic
+ * medium split into a homogeneous isotropic background (lambda0, mu0, rho0)
+ * and per-voxel contrasts dC (Voigt 6x6) and drho (Sec. 2, Eqs. 2-3, 8, 11):
+ *
+ *     A u = u - G * ( D.sigma + w^2 drho u ) = u0,   sigma_J = dC_JK eps_K(u),
+ *
+ * with eps the finite-difference Voigt strain (Eq. 18), D the central
+ * difference divergence, G the sampled background Green's tensor and "*" a
+ * zero-padded 3-D convolution evaluated by FFT (Eq. 21).  u0 is the
+ * background field of a moment-tensor point source (Eqs. 13-16).  A u = u0
+ * is solved with BiCGSTAB and the relative residual of Eq. 22.
+ *
+ * Conventions shared by every entry point:
+ *   - grid n = {nx, ny, nz}; node (ix, iy, iz) sits at (ix, iy, iz) * dx metres;
+ *   - a displacement field is 3 complex components, layout [c][iz][iy][ix]
+ *     (x fastest), complex numbers interleaved (re, im): complex128 (16 B)
+ *     unless an entry point says complex64;
+ *   - dC is 21 planes of float64, layout [k][iz][iy][ix], k running over the
+ *     upper triangle of the symmetric Voigt matrix row by row:
+ *     (1,1),(1,2),...,(1,6),(2,2),...,(6,6); Voigt order 11,22,33,23,13,12
+ *     (Sec. 3.1, Eq. 17); drho is one float64 plane [iz][iy][ix];
+ *   - moment tensors are Voigt 6-vectors (M11, M22, M33, M23, M13, M12);
+ *   - time dependence exp(-i w t): outgoing waves are exp(+i w r / c);
+ *   - every pointer argument named as "device" must be CUDA device memory of
+ *     the current device; the library never writes to caller inputs;
+ *   - calls are ordered on the handle's stream and asynchronous with respect
+ *     to the host unless they return host values (lsm_solve*, which
+ *     synchronise that stream before returning);
+ *   - errors are returned as lsm_status codes; no entry point aborts or traps;
+ *     lsm_last_error() describes the most recent failure of a handle.
+ *
+ * Every path runs in hand-written CUDA kernels (sm_103a).  Nothing here
+ * calls cuFFT or cuBLAS.
+ */
+#ifndef LSM_H
+#define LSM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsm_ctx *lsm_t;
+
+typedef enum {
+    LSM_OK = 0,
+    LSM_ERR_ARG = -1,        /* invalid argument (null pointer, size, unsupported grid) */
+    LSM_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    LSM_ERR_OOM = -3,        /* device allocation failed */
+    LSM_ERR_BREAKDOWN = -4,  /* BiCGSTAB breakdown (rho, omega or <r^,v> vanished or non-finite) */
+    LSM_ERR_NOCONV = -5,     /* iteration limit reached; the last iterate is returned */
+    LSM_ERR_TIMEOUT = -6,    /* reserved for bounded device waits */
+    LSM_WARN_SOURCE_ON_NODE = 1 /* lsm_source: a node coincides with the source; u0 = 0 there */
+} lsm_status;
+
+enum { LSM_FP64 = 0, LSM_MIXED = 1 };
+enum { LSM_GREEN_EXACT = 0, LSM_GREEN_PAPER = 1 };
+
+typedef struct {
+    int precision;     /* LSM_FP64: complex128 throughout.
+                          LSM_MIXED: complex64 FFTs/contractions with an FP64 outer
+                          residual and iterative refinement; FP64 inner products. */
+    int green;         /* LSM_GREEN_EXACT: full isotropic solution of Eq. 7 (default).
+                          LSM_GREEN_PAPER: near field Eq. A.4 + far field Eq. A.5. */
+    double tol;        /* target relative residual of Eq. 22 (default 1e-10) */
+    int maxit;         /* BiCGSTAB iteration limit per solve (FP64) or per inner solve (mixed) */
+    double inner_tol;  /* mixed: relative tolerance of each FP32 inner solve (default 1e-4) */
+    int max_outer;     /* mixed: refinement steps limit (default 8) */
+} lsm_opts;
+
+/* Fill *o with the defaults listed above.  o: host pointer, not null. */
+void lsm_default_opts(lsm_opts *o);
+
+/*
+ * Create a handle for one medium at one angular frequency omega [rad/s].
+ * Sec. 2 (Eqs. 2-3) defines the split into background and contrast;
+ * Appendix A and Eq. 21 define the Green's tensor whose spectrum is built here.
+ *
+ *   out      host pointer receiving the handle (set to NULL on failure)
+ *   n        host int[3] = {nx, ny, nz}; each n_a >= 2 and 2 n_a must factor into
+ *            2, 3 and 5 with 2 n_a <= 1024
+ *   dx       grid spacing [m], > 0
+ *   lambda0, mu0, rho0  background Lame parameters [Pa] and density [kg/m^3], mu0 > 0,
+ *            lambda0 + 2 mu0 > 0, rho0 > 0
+ *   dC       device float64, 21 * nz*ny*nx values (layout above); copied
+ *   drho     device float64, nz*ny*nx values; copied
+ *   omega    angular frequency [rad/s], > 0
+ *   opts     host pointer or NULL for defaults
+ *   stream   cudaStream_t (as void*) all work of this handle is ordered on; NULL = legacy default
+ *
+ * The library owns copies of the contrast (FP64, plus FP32 in LSM_MIXED), the
+ * octant-symmetric Green spectrum, and the workspaces.  Synchronises the
+ * stream before returning (setup only).
+ */
+lsm_status lsm_create(lsm_t *out, const int n[3], double dx,
+                      double lambda0, double mu0, double rho0,
+                      const double *dC, const double *drho,
+                      double omega, const lsm_opts *opts, void *stream);
+
+/*
+ * Create a handle for the medium of `base` at another angular frequency.
+ * The contrast storage is shared (reference counted) with `base`; the new
+ * handle builds its own Green spectrum (Eq. 21) and workspaces.  Same
+ * options and stream as `base`.  Handles sharing a medium may be solved
+ * together by lsm_solve_batched.
+ */
+lsm_status lsm_create_shared(lsm_t *out, lsm_t base, double omega);
+
+/*
+ * Background field of a moment-tensor point source (Eqs. 13-16, t0 = 0):
+ *   u0_i(x) = -M_jk dG_ij/dx_k (x - xs).
+ *   M   host double[6], Voigt (M11, M22, M33, M23, M13, M12)
+ *   xs  host double[3], source position [m]
+ *   u0  device complex128, 3 * nz*ny*nx (written)
+ * Returns LSM_WARN_SOURCE_ON_NODE (and u0 = 0 on that node, the cell
+ * average of an odd function) when a node coincides with xs.  Synchronises
+ * the handle's stream to read that flag.
+ */
+lsm_status lsm_source(lsm_t h, const double M[6], const double xs[3], void *u0);
+
+/*
+ * One application of the LS operator (Eqs. 19-21): Au = A u in FP64.
+ *   u, Au  device complex128, 3 * nz*ny*nx; u != Au required (no aliasing).
+ */
+lsm_status lsm_apply(lsm_t h, const void *u, void *Au);
+
+/*
+ * The same operator in FP32 arithmetic (complex64 FFTs and contraction):
+ *   u, Au  device complex64, 3 * nz*ny*nx; u != Au.
+ * Only for handles created with LSM_MIXED (else LSM_ERR_ARG).
+ */
+lsm_status lsm_apply_c64(lsm_t h, const void *u, void *Au);
+
+/*
+ * Adjoint operator A^H v in FP64 (the transposes of the apply's steps in
+ * reverse order: conjugate Green spectrum, conjugate derivative factors,
+ * transposed contrast and strain maps).
+ *   v, AHv  device complex128, 3 * nz*ny*nx; v != AHv.
+ */
+lsm_status lsm_adjoint(lsm_t h, const void *v, void *AHv);
+
+/*
+ * Solve A x = b with BiCGSTAB (Sec. 3.2) to the handle's tolerance on the
+ * relative residual of Eq. 22.
+ *   b       device complex128, 3 * nz*ny*nx (right-hand side, e.g. lsm_source's u0)
+ *   x       device complex128, 3 * nz*ny*nx; on entry the initial guess (zeros for
+ *           none), on exit the solution (the last iterate on LSM_ERR_NOCONV)
+ *   iters   host int* or NULL: BiCGSTAB iterations (mixed: total inner iterations)
+ *   relres  host double* or NULL: true FP64 residual ||b - A x|| / ||b|| at exit
+ * Synchronises the handle's stream.
+ */
+lsm_status lsm_solve(lsm_t h, const void *b, void *x, int *iters, double *relres);
+
+/*
+ * Solve nsys independent systems together (frequencies x sources).  All
+ * handles must share one medium (lsm_create_shared) and one precision;
+ * systems that use the same handle share its Green spectrum.  Each kernel
+ * of the solve runs over all unconverged systems in one launch; converged
+ * systems are masked out.
+ *   hs      host array of nsys handles (repeats allowed)
+ *   b, x    host arrays of nsys device pointers, as in lsm_solve
+ *   iters, relres, status  host arrays of nsys entries, or NULL
+ * Returns LSM_OK when every system converged, else the first failing status.
+ */
+lsm_status lsm_solve_batched(int nsys, const lsm_t *hs, const void *const *b, void *const *x,
+                             int *iters, double *relres, lsm_status *status);
+
+/* Number of kernel launches the library has issued on this handle (diagnostics). */
+long long lsm_launch_count(lsm_t h);
+
+/* Release every device buffer the handle owns (shared contrast when its last user goes). */
+void lsm_destroy(lsm_t h);
+
+/* Text of the most recent error on h (or of the last failed create when h is NULL). */
+const char *lsm_last_error(lsm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSM_H */

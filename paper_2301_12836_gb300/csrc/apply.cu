@@ -1,0 +1,766 @@
+// apply.cu - the matrix-free Lippmann-Schwinger operator (Eqs. 8, 11, 18-21) and its adjoint.
+//
+// One application A u = u - crop( G * q ), q_j = sum_k D_k sigma_jk + w^2 drho u_j, runs as:
+//   k_stress      eps (Eq. 18, one-sided on boundary nodes) -> sigma_J = dC_JK eps_K (Eq. 11)
+//   k_div_fftx    q on the extended nodes [-1, n] (central-difference divergence of sigma plus
+//                 the density term), zero-padded to 2 n_x and FFT'd along x
+//   k_strided     forward FFT along y (zero padding pruned on load)
+//   k_fftz_green  forward FFT along z, u-hat_i = sum_j G-hat_ij q-hat_j, inverse FFT along z, crop
+//   k_strided     inverse FFT along y, crop
+//   k_fftx_out    inverse FFT along x, crop, Au = u - u_s
+// Only three displacement-like components pass through the FFTs: the derivative of the
+// Green tensor in Eq. 8 is applied as the central difference D_k in real space, which is
+// exactly the factor i sin(k h)/h of the spectral form.  The contrast source q is shifted by
+// one node (index p holds node p - 1) so that it occupies [0, n+2) of the 2n-periodic grid;
+// the result is then read at indices 1..n.  1/P of the inverse FFT is folded into G-hat.
+#include "kernels.h"
+#include "fft.cuh"
+
+namespace lsm {
+
+static constexpr int NTH = 256;
+
+// Voigt index (order 11, 22, 33, 23, 13, 12) of the tensor pair (j, k).
+__device__ __forceinline__ int t2v(int j, int k) { return (j == k) ? j : (6 - j - k); }
+
+// index of Voigt (I, J), I <= J, in the 21 packed planes (upper triangle, row-major)
+__host__ __device__ __forceinline__ int p21(int I, int J) {
+    if (I > J) { int t = I; I = J; J = t; }
+    return I * 6 - (I * (I - 1)) / 2 + (J - I);
+}
+
+template <typename C>
+__device__ __forceinline__ void ghat_at(const C* __restrict__ g, const Dims& d, int kx, int ky, int kz,
+                                        bool conj, C G[6]) {
+    typedef typename real_of<C>::type T;
+    const int fx = kx <= d.nx ? kx : d.Lx - kx;
+    const int fy = ky <= d.ny ? ky : d.Ly - ky;
+    const int fz = kz <= d.nz ? kz : d.Lz - kz;
+    const T sx = kx > d.nx ? (T)-1 : (T)1;
+    const T sy = ky > d.ny ? (T)-1 : (T)1;
+    const T sz = kz > d.nz ? (T)-1 : (T)1;
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long i = ((long long)fz * (d.ny + 1) + fy) * (d.nx + 1) + fx;
+    G[0] = __ldg(&g[i]);
+    G[1] = __ldg(&g[NO + i]);
+    G[2] = __ldg(&g[2 * NO + i]);
+    G[3] = cscale(__ldg(&g[3 * NO + i]), sy * sz);
+    G[4] = cscale(__ldg(&g[4 * NO + i]), sx * sz);
+    G[5] = cscale(__ldg(&g[5 * NO + i]), sx * sy);
+    if (conj) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) G[c] = cconj(G[c]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// strain + contraction
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_stress(Dims d, const T* __restrict__ dC, const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    const C* __restrict__ u = S.u;
+    C* __restrict__ sig = S.w1;
+    const long long N = d.N;
+    const T ih = (T)(1.0 / d.h), i2h = (T)(0.5 / d.h);
+    const long long sxy = (long long)d.nx * d.ny;
+    for (long long idx = (long long)blockIdx.x * NTH + threadIdx.x; idx < N; idx += (long long)gridDim.x * NTH) {
+        const int ix = (int)(idx % d.nx);
+        const int iy = (int)((idx / d.nx) % d.ny);
+        const int iz = (int)(idx / sxy);
+        auto der = [&](int c, int a) -> C {
+            const C* f = u + c * N;
+            const int i = a == 0 ? ix : (a == 1 ? iy : iz);
+            const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
+            const long long s = a == 0 ? 1 : (a == 1 ? (long long)d.nx : sxy);
+            if (i == 0) return cscale(csub(f[idx + s], f[idx]), ih);
+            if (i == n - 1) return cscale(csub(f[idx], f[idx - s]), ih);
+            return cscale(csub(f[idx + s], f[idx - s]), i2h);
+        };
+        C e[6];
+        e[0] = der(0, 0);
+        e[1] = der(1, 1);
+        e[2] = der(2, 2);
+        e[3] = cadd(der(1, 2), der(2, 1));
+        e[4] = cadd(der(0, 2), der(2, 0));
+        e[5] = cadd(der(0, 1), der(1, 0));
+        T c21[21];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) c21[k] = __ldg(&dC[k * N + idx]);
+#pragma unroll
+        for (int J = 0; J < 6; ++J) {
+            C s = czero<C>();
+#pragma unroll
+            for (int K = 0; K < 6; ++K) {
+                const T c = c21[p21(J, K)];
+                s.x += c * e[K].x;
+                s.y += c * e[K].y;
+            }
+            sig[J * N + idx] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// contrast source q (extended nodes) + forward FFT along x.  CTA: B rows y' at one z', 3 comps.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_div_fftx(Dims d, const T* __restrict__ drho, const ApplySys<T>* __restrict__ sys,
+                                                  FftPlan px, const typename cplx_of<T>::type* __restrict__ tw, int B) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    const ApplySys<T> S = sys[blockIdx.z];
+    if (S.run && !*S.run) return;
+    const int NL = 3 * B, LD = NL + 1, L = d.Lx;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)L * LD;
+    const int zp = blockIdx.y;            // extended z index; node z = zp - 1
+    const int y0 = blockIdx.x * B;
+    const long long N = d.N;
+    const long long sxy = (long long)d.nx * d.ny;
+    const C* __restrict__ sig = S.w1;
+    const C* __restrict__ u = S.u;
+    const T i2h = (T)(0.5 / d.h);
+    const int pz = zp - 1;
+    for (int i = threadIdx.x; i < NL * L; i += NTH) {
+        const int xp = i % L;
+        const int l = i / L;
+        const int j = l / B;
+        const int yp = y0 + (l % B);
+        C q = czero<C>();
+        if (xp < d.ex && yp < d.ey) {
+            const int p[3] = {xp - 1, yp - 1, pz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const C* sJ = sig + (long long)t2v(j, k) * N;
+                int a[3] = {p[0], p[1], p[2]};
+                a[k] += 1;
+                if (a[0] >= 0 && a[0] < d.nx && a[1] >= 0 && a[1] < d.ny && a[2] >= 0 && a[2] < d.nz)
+                    q = cadd(q, sJ[a[2] * sxy + (long long)a[1] * d.nx + a[0]]);
+                a[k] -= 2;
+                if (a[0] >= 0 && a[0] < d.nx && a[1] >= 0 && a[1] < d.ny && a[2] >= 0 && a[2] < d.nz)
+                    q = csub(q, sJ[a[2] * sxy + (long long)a[1] * d.nx + a[0]]);
+            }
+            q = cscale(q, i2h);
+            if (p[0] >= 0 && p[0] < d.nx && p[1] >= 0 && p[1] < d.ny && p[2] >= 0 && p[2] < d.nz) {
+                const long long idx = p[2] * sxy + (long long)p[1] * d.nx + p[0];
+                const T w = S.omega2 * __ldg(&drho[idx]);
+                const C uj = u[j * N + idx];
+                q.x += w * uj.x;
+                q.y += w * uj.y;
+            }
+        }
+        sa[xp * LD + l] = q;
+    }
+    __syncthreads();
+    C* r = fft_smem<-1>(sa, sb, px, NL, LD, tw, threadIdx.x, NTH);
+    C* __restrict__ out = S.w2;  // [3][ez][ey][Lx]
+    for (int i = threadIdx.x; i < NL * L; i += NTH) {
+        const int kx = i % L;
+        const int l = i / L;
+        const int j = l / B;
+        const int yp = y0 + (l % B);
+        if (yp < d.ey) out[(((long long)j * d.ez + zp) * d.ey + yp) * L + kx] = r[kx * LD + l];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// generic strided pass: TX consecutive lines (along x) of a strided axis.  Element e of line x of
+// outer (oy = blockIdx.y, comp c) lives at base + c*os2 + oy*os1 + e*es + x.
+// ---------------------------------------------------------------------------------------------
+struct StridedArgs {
+    int nlines;        // lines along x (row length of src and dst)
+    int TX;
+    int in_count, in_off, out_count, out_off;
+    long long src_es, src_os1, src_os2;
+    long long dst_es, dst_os1, dst_os2;
+    int ncomp;         // comps per system (blockIdx.z = c + ncomp * sys)
+    int src_sel, dst_sel;  // 0 u, 1 out, 2 w1, 3 w2
+};
+
+template <typename C>
+__device__ __forceinline__ C* pick(const ApplySys<typename real_of<C>::type>& S, int sel) {
+    switch (sel) {
+        case 0: return const_cast<C*>(S.u);
+        case 1: return S.out;
+        case 2: return S.w1;
+        default: return S.w2;
+    }
+}
+
+template <int DIR, typename C>
+__device__ __forceinline__ void strided_tile(const C* src, C* dst, const FftPlan& p, const C* __restrict__ tw,
+                                             const StridedArgs& a, int x0, C* sa, C* sb) {
+    const int L = p.L, TX = a.TX;
+    for (int i = threadIdx.x; i < L * TX; i += NTH) {
+        const int l = i % TX;
+        const int e = i / TX;
+        const int x = x0 + l;
+        const int es = e - a.in_off;
+        C v = czero<C>();
+        if (x < a.nlines && es >= 0 && es < a.in_count) v = src[es * a.src_es + x];
+        sa[i] = v;
+    }
+    __syncthreads();
+    C* r = fft_smem<DIR>(sa, sb, p, TX, TX, tw, threadIdx.x, NTH);
+    for (int i = threadIdx.x; i < a.out_count * TX; i += NTH) {
+        const int l = i % TX;
+        const int eo = i / TX;
+        const int x = x0 + l;
+        if (x < a.nlines) dst[eo * a.dst_es + x] = r[(eo + a.out_off) * TX + l];
+    }
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(NTH) k_strided(FftPlan p, const typename cplx_of<T>::type* __restrict__ tw,
+                                                 StridedArgs a, const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    const int c = blockIdx.z % a.ncomp;
+    const int s = blockIdx.z / a.ncomp;
+    const ApplySys<T> S = sys[s];
+    if (S.run && !*S.run) return;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)p.L * a.TX;
+    const C* src = pick<C>(S, a.src_sel) + c * a.src_os2 + blockIdx.y * a.src_os1;
+    C* dst = pick<C>(S, a.dst_sel) + c * a.dst_os2 + blockIdx.y * a.dst_os1;
+    strided_tile<DIR>(src, dst, p, tw, a, blockIdx.x * a.TX, sa, sb);
+}
+
+// raw-pointer variant for the Green spectrum setup (in place allowed: each CTA owns its tile)
+template <typename T, int DIR>
+__global__ void __launch_bounds__(NTH) k_strided_raw(FftPlan p, const typename cplx_of<T>::type* __restrict__ tw,
+                                                     StridedArgs a, const typename cplx_of<T>::type* src0,
+                                                     typename cplx_of<T>::type* dst0) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)p.L * a.TX;
+    const C* src = src0 + blockIdx.z * a.src_os2 + blockIdx.y * a.src_os1;
+    C* dst = dst0 + blockIdx.z * a.dst_os2 + blockIdx.y * a.dst_os1;
+    strided_tile<DIR>(src, dst, p, tw, a, blockIdx.x * a.TX, sa, sb);
+}
+
+// ---------------------------------------------------------------------------------------------
+// z pass with the Green multiply: forward z FFT, u-hat = G-hat q-hat (conj G-hat for the
+// adjoint), inverse z FFT.  CTA: TX lines along x at one ky, all three components.
+// src [3][in_count][Ly][Lx] (sel), dst [3][out_count][Ly][Lx] (sel)
+// ---------------------------------------------------------------------------------------------
+template <typename T, bool CONJ>
+__global__ void __launch_bounds__(NTH) k_fftz_green(Dims d, FftPlan pz, const typename cplx_of<T>::type* __restrict__ tw,
+                                                    const ApplySys<T>* __restrict__ sys, int TX, int in_count, int in_off,
+                                                    int out_count, int out_off, int src_sel, int dst_sel) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    const ApplySys<T> S = sys[blockIdx.z];
+    if (S.run && !*S.run) return;
+    const int L = d.Lz, NL = 3 * TX;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)L * NL;
+    const int ky = blockIdx.y;
+    const int x0 = blockIdx.x * TX;
+    const long long plane = (long long)d.Ly * d.Lx;
+    const C* src = pick<C>(S, src_sel);
+    C* dst = pick<C>(S, dst_sel);
+    const long long s_c = (long long)in_count * plane, d_c = (long long)out_count * plane;
+    for (int i = threadIdx.x; i < L * NL; i += NTH) {
+        const int lx = i % TX;
+        const int rest = i / TX;
+        const int c = rest % 3;
+        const int e = rest / 3;
+        const int x = x0 + lx;
+        const int es = e - in_off;
+        C v = czero<C>();
+        if (x < d.Lx && es >= 0 && es < in_count) v = src[c * s_c + es * plane + (long long)ky * d.Lx + x];
+        sa[e * NL + c * TX + lx] = v;
+    }
+    __syncthreads();
+    C* r = fft_smem<-1>(sa, sb, pz, NL, NL, tw, threadIdx.x, NTH);
+    C* o = (r == sa) ? sb : sa;
+    for (int i = threadIdx.x; i < L * TX; i += NTH) {
+        const int lx = i % TX;
+        const int kz = i / TX;
+        const int kx = x0 + lx;
+        if (kx >= d.Lx) continue;
+        C G[6];
+        ghat_at(S.ghat, d, kx, ky, kz, CONJ, G);
+        C* row = r + kz * NL + lx;
+        const C q0 = row[0], q1 = row[TX], q2 = row[2 * TX];
+        row[0] = cadd(cadd(cmul(G[0], q0), cmul(G[5], q1)), cmul(G[4], q2));
+        row[TX] = cadd(cadd(cmul(G[5], q0), cmul(G[1], q1)), cmul(G[3], q2));
+        row[2 * TX] = cadd(cadd(cmul(G[4], q0), cmul(G[3], q1)), cmul(G[2], q2));
+    }
+    __syncthreads();
+    C* r2 = fft_smem<1>(r, o, pz, NL, NL, tw, threadIdx.x, NTH);
+    for (int i = threadIdx.x; i < out_count * NL; i += NTH) {
+        const int lx = i % TX;
+        const int rest = i / TX;
+        const int c = rest % 3;
+        const int eo = rest / 3;
+        const int x = x0 + lx;
+        if (x < d.Lx) dst[c * d_c + eo * plane + (long long)ky * d.Lx + x] = r2[(eo + out_off) * NL + c * TX + lx];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// inverse FFT along x + crop + Au = u - u_s.  CTA: B rows y at one z, 3 comps.  src w1 [3][nz][ny][Lx]
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys, FftPlan px,
+                                                  const typename cplx_of<T>::type* __restrict__ tw, int B) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    const ApplySys<T> S = sys[blockIdx.z];
+    if (S.run && !*S.run) return;
+    const int NL = 3 * B, LD = NL + 1, L = d.Lx;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)L * LD;
+    const int z = blockIdx.y;
+    const int y0 = blockIdx.x * B;
+    const C* __restrict__ src = S.w1;
+    for (int i = threadIdx.x; i < NL * L; i += NTH) {
+        const int kx = i % L;
+        const int l = i / L;
+        const int c = l / B;
+        const int y = y0 + (l % B);
+        C v = czero<C>();
+        if (y < d.ny) v = src[(((long long)c * d.nz + z) * d.ny + y) * L + kx];
+        sa[kx * LD + l] = v;
+    }
+    __syncthreads();
+    C* r = fft_smem<1>(sa, sb, px, NL, LD, tw, threadIdx.x, NTH);
+    for (int i = threadIdx.x; i < NL * d.nx; i += NTH) {
+        const int x = i % d.nx;
+        const int l = i / d.nx;
+        const int c = l / B;
+        const int y = y0 + (l % B);
+        if (y < d.ny) {
+            const long long idx = (((long long)c * d.nz + z) * d.ny + y) * d.nx + x;
+            S.out[idx] = csub(S.u[idx], r[(x + 1) * LD + l]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// generic contiguous-rows pass: NL rows per CTA.  Row r of src starts at src + r*in_count (elements
+// placed at in_off), row r of dst at dst + r*out_count (elements read from out_off).
+// ---------------------------------------------------------------------------------------------
+template <int DIR, typename C>
+__device__ __forceinline__ void rows_tile(const C* src, C* dst, const FftPlan& p, const C* __restrict__ tw,
+                                          long long r0, long long nrows, int NL, int in_count, int in_off,
+                                          int out_count, int out_off, C* sa, C* sb) {
+    const int L = p.L, LD = NL + 1;
+    for (int i = threadIdx.x; i < NL * L; i += NTH) {
+        const int e = i % L;
+        const int l = i / L;
+        const long long row = r0 + l;
+        const int es = e - in_off;
+        C v = czero<C>();
+        if (row < nrows && es >= 0 && es < in_count) v = src[row * in_count + es];
+        sa[e * LD + l] = v;
+    }
+    __syncthreads();
+    C* r = fft_smem<DIR>(sa, sb, p, NL, LD, tw, threadIdx.x, NTH);
+    for (int i = threadIdx.x; i < NL * out_count; i += NTH) {
+        const int e = i % out_count;
+        const int l = i / out_count;
+        const long long row = r0 + l;
+        if (row < nrows) dst[row * out_count + e] = r[(e + out_off) * LD + l];
+    }
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(NTH) k_rows(FftPlan p, const typename cplx_of<T>::type* __restrict__ tw,
+                                              const ApplySys<T>* __restrict__ sys, int src_sel, int dst_sel,
+                                              long long nrows, int NL, int in_count, int in_off, int out_count, int out_off) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)p.L * (NL + 1);
+    rows_tile<DIR>(pick<C>(S, src_sel), pick<C>(S, dst_sel), p, tw, (long long)blockIdx.x * NL, nrows, NL,
+                   in_count, in_off, out_count, out_off, sa, sb);
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(NTH) k_rows_raw(FftPlan p, const typename cplx_of<T>::type* __restrict__ tw,
+                                                  const typename cplx_of<T>::type* src, typename cplx_of<T>::type* dst,
+                                                  long long nrows, int NL) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = sa + (size_t)p.L * (NL + 1);
+    rows_tile<DIR>(src, dst, p, tw, (long long)blockIdx.x * NL, nrows, NL, p.L, 0, p.L, 0, sa, sb);
+}
+
+// ---------------------------------------------------------------------------------------------
+// adjoint: transposed divergence and contraction.  z (extended nodes) in w1 [3][ez][ey][ex];
+// writes c_K = sum_J dC_JK tau_J into w2 [6][N], tau_J = sum_{(j,k)->J} D_k^T z_j.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_adj_stress(Dims d, const T* __restrict__ dC, const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    const C* __restrict__ z = S.w1;
+    C* __restrict__ cc = S.w2;
+    const long long N = d.N;
+    const long long E = (long long)d.ex * d.ey * d.ez;
+    const T i2h = (T)(0.5 / d.h);
+    const long long sxy = (long long)d.nx * d.ny;
+    for (long long idx = (long long)blockIdx.x * NTH + threadIdx.x; idx < N; idx += (long long)gridDim.x * NTH) {
+        const int ix = (int)(idx % d.nx);
+        const int iy = (int)((idx / d.nx) % d.ny);
+        const int iz = (int)(idx / sxy);
+        // extended index of node (ix, iy, iz) is (ix+1, iy+1, iz+1)
+        const long long e0 = ((long long)(iz + 1) * d.ey + (iy + 1)) * d.ex + (ix + 1);
+        const long long st[3] = {1, (long long)d.ex, (long long)d.ex * d.ey};
+        C tau[6];
+#pragma unroll
+        for (int J = 0; J < 6; ++J) tau[J] = czero<C>();
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const C* zj = z + j * E;
+                const C v = csub(zj[e0 - st[k]], zj[e0 + st[k]]);
+                const int J = t2v(j, k);
+                tau[J] = cadd(tau[J], v);
+            }
+        }
+        T c21[21];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) c21[k] = __ldg(&dC[k * N + idx]);
+#pragma unroll
+        for (int K = 0; K < 6; ++K) {
+            C s = czero<C>();
+#pragma unroll
+            for (int J = 0; J < 6; ++J) {
+                const T c = c21[p21(J, K)];
+                s.x += c * tau[J].x;
+                s.y += c * tau[J].y;
+            }
+            cc[K * N + idx] = cscale(s, i2h);
+        }
+    }
+}
+
+// transpose of the Eq. 18 derivative along one axis, at node i of n, for field f with stride s
+template <typename C, typename T>
+__device__ __forceinline__ C dT_axis(const C* f, long long idx, int i, int n, long long s, T ih, T i2h) {
+    C acc = czero<C>();
+    // interior rows i-1 and i+1 (rows 1..n-2 use the central difference)
+    if (i - 1 >= 1 && i - 1 <= n - 2) acc = cadd(acc, cscale(f[idx - s], i2h));
+    if (i + 1 >= 1 && i + 1 <= n - 2) acc = csub(acc, cscale(f[idx + s], i2h));
+    // boundary row 0: (f1 - f0)/h
+    if (i == 0) acc = csub(acc, cscale(f[idx], ih));
+    if (i == 1) acc = cadd(acc, cscale(f[idx - s], ih));
+    // boundary row n-1: (f_{n-1} - f_{n-2})/h
+    if (i == n - 2) acc = csub(acc, cscale(f[idx + s], ih));
+    if (i == n - 1) acc = cadd(acc, cscale(f[idx], ih));
+    return acc;
+}
+
+// AH w = w - (E^T c + w^2 drho z)
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_adj_out(Dims d, const T* __restrict__ drho, const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    const C* __restrict__ cc = S.w2;
+    const C* __restrict__ z = S.w1;
+    const long long N = d.N;
+    const long long E = (long long)d.ex * d.ey * d.ez;
+    const T ih = (T)(1.0 / d.h), i2h = (T)(0.5 / d.h);
+    const long long sxy = (long long)d.nx * d.ny;
+    for (long long idx = (long long)blockIdx.x * NTH + threadIdx.x; idx < N; idx += (long long)gridDim.x * NTH) {
+        const int ix = (int)(idx % d.nx);
+        const int iy = (int)((idx / d.nx) % d.ny);
+        const int iz = (int)(idx / sxy);
+        const int ii[3] = {ix, iy, iz};
+        const int nn[3] = {d.nx, d.ny, d.nz};
+        const long long ss[3] = {1, (long long)d.nx, sxy};
+        const long long e0 = ((long long)(iz + 1) * d.ey + (iy + 1)) * d.ex + (ix + 1);
+        const T w = S.omega2 * __ldg(&drho[idx]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            C acc = czero<C>();
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc = cadd(acc, dT_axis(cc + (long long)t2v(i, a) * N, idx, ii[a], nn[a], ss[a], ih, i2h));
+            const C zi = z[i * E + e0];
+            acc.x += w * zi.x;
+            acc.y += w * zi.y;
+            S.out[i * N + idx] = csub(S.u[i * N + idx], acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------------
+void apply_ws_elems(const Dims& d, long long* w1, long long* w2) {
+    const long long N = d.N;
+    const long long sig = 6 * N;
+    const long long y1 = 3LL * d.ez * d.Ly * d.Lx;
+    const long long y2 = 3LL * d.nz * d.ny * d.Lx;
+    const long long adjz = 3LL * d.ez * d.ey * d.ex;
+    const long long adjw1a = 3LL * d.nz * d.ny * d.Lx;
+    long long a = sig > y1 ? sig : y1;
+    a = a > y2 ? a : y2;
+    a = a > adjz ? a : adjz;
+    a = a > adjw1a ? a : adjw1a;
+    const long long x1 = 3LL * d.ez * d.ey * d.Lx;
+    const long long z1 = 3LL * d.nz * d.Ly * d.Lx;
+    const long long adjw2 = 3LL * d.ez * d.ey * d.Lx;
+    long long b = x1 > z1 ? x1 : z1;
+    b = b > sig ? b : sig;
+    b = b > adjw2 ? b : adjw2;
+    *w1 = a;
+    *w2 = b;
+}
+
+static const size_t SMEM_CAP = 96 * 1024;
+
+template <typename T>
+static int rows_per_tile(int L) {
+    typedef typename cplx_of<T>::type C;
+    // 3 comps x B rows, ping-pong, padded leading dimension
+    int B = 8;
+    while (B > 1 && 2 * (size_t)L * (3 * B + 1) * sizeof(C) > SMEM_CAP) --B;
+    return B;
+}
+template <typename T>
+static int strided_tx(int L, int ncomp) {
+    typedef typename cplx_of<T>::type C;
+    int TX = sizeof(T) == 4 ? 16 : 8;
+    while (TX > 1 && 2 * (size_t)L * ncomp * TX * sizeof(C) > SMEM_CAP) TX /= 2;
+    return TX;
+}
+template <typename T>
+static int generic_rows_nl(int L) {
+    typedef typename cplx_of<T>::type C;
+    int NL = 16;
+    while (NL > 1 && 2 * (size_t)L * (NL + 1) * sizeof(C) > SMEM_CAP) NL /= 2;
+    return NL;
+}
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+static inline int grid_elems(long long n) {
+    long long b = (n + NTH - 1) / NTH;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
+                         long long* nl) {
+    typedef typename cplx_of<T>::type C;
+    const Dims& d = m.d;
+    const T* dC = (const T*)m.dC;
+    const T* drho = (const T*)m.drho;
+    const C* twx = (const C*)pl.twx;
+    const C* twy = (const C*)pl.twy;
+    const C* twz = (const C*)pl.twz;
+    // 1. strain + contraction
+    k_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
+    // 2. contrast source + forward x FFT -> w2 [3][ez][ey][Lx]
+    {
+        const int B = rows_per_tile<T>(d.Lx);
+        const size_t sm = 2 * (size_t)d.Lx * (3 * B + 1) * sizeof(C);
+        k_div_fftx<T><<<dim3(cdiv(d.ey, B), d.ez, nsys), NTH, sm, st>>>(d, drho, sys, pl.px, twx, B);
+    }
+    // 3. forward y FFT: w2 [3][ez][ey][Lx] -> w1 [3][ez][Ly][Lx]
+    {
+        StridedArgs a;
+        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
+        a.in_count = d.ey; a.in_off = 0; a.out_count = d.Ly; a.out_off = 0;
+        a.src_es = d.Lx; a.src_os1 = (long long)d.ey * d.Lx; a.src_os2 = (long long)d.ez * d.ey * d.Lx;
+        a.dst_es = d.Lx; a.dst_os1 = (long long)d.Ly * d.Lx; a.dst_os2 = (long long)d.ez * d.Ly * d.Lx;
+        a.ncomp = 3; a.src_sel = 3; a.dst_sel = 2;
+        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        k_strided<T, -1><<<dim3(cdiv(d.Lx, a.TX), d.ez, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
+    }
+    // 4. z FFT, Green multiply, inverse z FFT, crop: w1 [3][ez][Ly][Lx] -> w2 [3][nz][Ly][Lx]
+    {
+        const int TX = strided_tx<T>(d.Lz, 3);
+        const size_t sm = 2 * (size_t)d.Lz * 3 * TX * sizeof(C);
+        k_fftz_green<T, false><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), NTH, sm, st>>>(d, pl.pz, twz, sys, TX, d.ez, 0, d.nz, 1, 2, 3);
+    }
+    // 5. inverse y FFT + crop: w2 [3][nz][Ly][Lx] -> w1 [3][nz][ny][Lx]
+    {
+        StridedArgs a;
+        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
+        a.in_count = d.Ly; a.in_off = 0; a.out_count = d.ny; a.out_off = 1;
+        a.src_es = d.Lx; a.src_os1 = (long long)d.Ly * d.Lx; a.src_os2 = (long long)d.nz * d.Ly * d.Lx;
+        a.dst_es = d.Lx; a.dst_os1 = (long long)d.ny * d.Lx; a.dst_os2 = (long long)d.nz * d.ny * d.Lx;
+        a.ncomp = 3; a.src_sel = 3; a.dst_sel = 2;
+        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        k_strided<T, 1><<<dim3(cdiv(d.Lx, a.TX), d.nz, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
+    }
+    // 6. inverse x FFT + crop + Au = u - u_s
+    {
+        const int B = rows_per_tile<T>(d.Lx);
+        const size_t sm = 2 * (size_t)d.Lx * (3 * B + 1) * sizeof(C);
+        k_fftx_out<T><<<dim3(cdiv(d.ny, B), d.nz, nsys), NTH, sm, st>>>(d, sys, pl.px, twx, B);
+    }
+    if (nl) *nl += 6;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
+                           long long* nl) {
+    typedef typename cplx_of<T>::type C;
+    const Dims& d = m.d;
+    const T* dC = (const T*)m.dC;
+    const T* drho = (const T*)m.drho;
+    const C* twx = (const C*)pl.twx;
+    const C* twy = (const C*)pl.twy;
+    const C* twz = (const C*)pl.twz;
+    // 1. w placed at x positions 1..nx, forward x FFT: u [3][nz][ny][nx] -> w1 [3][nz][ny][Lx]
+    {
+        const int NL = generic_rows_nl<T>(d.Lx);
+        const long long nrows = 3LL * d.nz * d.ny;
+        const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+        k_rows<T, -1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, twx, sys, 0, 2, nrows, NL, d.nx, 1, d.Lx, 0);
+    }
+    // 2. forward y FFT, input at 1..ny: w1 [3][nz][ny][Lx] -> w2 [3][nz][Ly][Lx]
+    {
+        StridedArgs a;
+        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
+        a.in_count = d.ny; a.in_off = 1; a.out_count = d.Ly; a.out_off = 0;
+        a.src_es = d.Lx; a.src_os1 = (long long)d.ny * d.Lx; a.src_os2 = (long long)d.nz * d.ny * d.Lx;
+        a.dst_es = d.Lx; a.dst_os1 = (long long)d.Ly * d.Lx; a.dst_os2 = (long long)d.nz * d.Ly * d.Lx;
+        a.ncomp = 3; a.src_sel = 2; a.dst_sel = 3;
+        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        k_strided<T, -1><<<dim3(cdiv(d.Lx, a.TX), d.nz, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
+    }
+    // 3. z: input at 1..nz, conj(G-hat), output extended 0..ez-1: w2 -> w1 [3][ez][Ly][Lx]
+    {
+        const int TX = strided_tx<T>(d.Lz, 3);
+        const size_t sm = 2 * (size_t)d.Lz * 3 * TX * sizeof(C);
+        k_fftz_green<T, true><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), NTH, sm, st>>>(d, pl.pz, twz, sys, TX, d.nz, 1, d.ez, 0, 3, 2);
+    }
+    // 4. inverse y FFT, keep 0..ey-1: w1 [3][ez][Ly][Lx] -> w2 [3][ez][ey][Lx]
+    {
+        StridedArgs a;
+        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
+        a.in_count = d.Ly; a.in_off = 0; a.out_count = d.ey; a.out_off = 0;
+        a.src_es = d.Lx; a.src_os1 = (long long)d.Ly * d.Lx; a.src_os2 = (long long)d.ez * d.Ly * d.Lx;
+        a.dst_es = d.Lx; a.dst_os1 = (long long)d.ey * d.Lx; a.dst_os2 = (long long)d.ez * d.ey * d.Lx;
+        a.ncomp = 3; a.src_sel = 2; a.dst_sel = 3;
+        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        k_strided<T, 1><<<dim3(cdiv(d.Lx, a.TX), d.ez, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
+    }
+    // 5. inverse x FFT, keep 0..ex-1: w2 [3][ez][ey][Lx] -> w1 [3][ez][ey][ex]
+    {
+        const int NL = generic_rows_nl<T>(d.Lx);
+        const long long nrows = 3LL * d.ez * d.ey;
+        const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+        k_rows<T, 1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, twx, sys, 3, 2, nrows, NL, d.Lx, 0, d.ex, 0);
+    }
+    // 6. transposed divergence + contraction -> w2 [6][N]
+    k_adj_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
+    // 7. transposed strain + density, AH w = w - (...)
+    k_adj_out<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, drho, sys);
+    if (nl) *nl += 7;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_apply<float>(const Medium&, const Plans&, const ApplySys<float>*, int, cudaStream_t, long long*);
+template cudaError_t launch_apply<double>(const Medium&, const Plans&, const ApplySys<double>*, int, cudaStream_t, long long*);
+template cudaError_t launch_adjoint<double>(const Medium&, const Plans&, const ApplySys<double>*, int, cudaStream_t, long long*);
+template cudaError_t launch_adjoint<float>(const Medium&, const Plans&, const ApplySys<float>*, int, cudaStream_t, long long*);
+
+// ---------------------------------------------------------------------------------------------
+// Green spectrum setup (FP64): 3-D FFT of the sampled table, in place, then octant extraction.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_extract_octant(Dims d, const double2* __restrict__ full, double2* __restrict__ oct, double scale) {
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long total = 6 * NO;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / NO);
+        long long r = i % NO;
+        const int fx = (int)(r % (d.nx + 1)); r /= (d.nx + 1);
+        const int fy = (int)(r % (d.ny + 1));
+        const int fz = (int)(r / (d.ny + 1));
+        const double2 v = full[(((long long)c * d.Lz + fz) * d.Ly + fy) * d.Lx + fx];
+        oct[i] = make_double2(v.x * scale, v.y * scale);
+    }
+}
+
+cudaError_t fft3_inplace_setup(const Dims& d, const Plans& pl, double2* buf, int ncomp, cudaStream_t st, long long* nl) {
+    typedef double2 C;
+    // x: rows
+    {
+        const int NL = generic_rows_nl<double>(d.Lx);
+        const long long nrows = (long long)ncomp * d.Lz * d.Ly;
+        const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+        k_rows_raw<double, -1><<<cdiv(nrows, NL), NTH, sm, st>>>(pl.px, (const C*)pl.twx, buf, buf, nrows, NL);
+    }
+    // y: lines along y, outer1 = z (Lz), comp
+    {
+        StridedArgs a;
+        a.nlines = d.Lx; a.TX = strided_tx<double>(d.Ly, 1);
+        a.in_count = d.Ly; a.in_off = 0; a.out_count = d.Ly; a.out_off = 0;
+        a.src_es = d.Lx; a.src_os1 = (long long)d.Ly * d.Lx; a.src_os2 = (long long)d.Lz * d.Ly * d.Lx;
+        a.dst_es = a.src_es; a.dst_os1 = a.src_os1; a.dst_os2 = a.src_os2;
+        a.ncomp = ncomp; a.src_sel = a.dst_sel = 0;
+        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        k_strided_raw<double, -1><<<dim3(cdiv(d.Lx, a.TX), d.Lz, ncomp), NTH, sm, st>>>(pl.py, (const C*)pl.twy, a, buf, buf);
+    }
+    // z: lines along z, outer1 = y (Ly), comp
+    {
+        StridedArgs a;
+        a.nlines = d.Lx; a.TX = strided_tx<double>(d.Lz, 1);
+        a.in_count = d.Lz; a.in_off = 0; a.out_count = d.Lz; a.out_off = 0;
+        a.src_es = (long long)d.Ly * d.Lx; a.src_os1 = d.Lx; a.src_os2 = (long long)d.Lz * d.Ly * d.Lx;
+        a.dst_es = a.src_es; a.dst_os1 = a.src_os1; a.dst_os2 = a.src_os2;
+        a.ncomp = ncomp; a.src_sel = a.dst_sel = 0;
+        const size_t sm = 2 * (size_t)d.Lz * a.TX * sizeof(C);
+        k_strided_raw<double, -1><<<dim3(cdiv(d.Lx, a.TX), d.Ly, ncomp), NTH, sm, st>>>(pl.pz, (const C*)pl.twz, a, buf, buf);
+    }
+    if (nl) *nl += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* oct, double scale, cudaStream_t st, long long* nl) {
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    k_extract_octant<<<grid_elems(6 * NO), NTH, 0, st>>>(d, full, oct, scale);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t init_kernel_attributes() {
+    const int cap = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+#define LSM_ATTR(K) if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
+    LSM_ATTR(k_div_fftx<float>);
+    LSM_ATTR(k_div_fftx<double>);
+    LSM_ATTR((k_strided<float, -1>));
+    LSM_ATTR((k_strided<float, 1>));
+    LSM_ATTR((k_strided<double, -1>));
+    LSM_ATTR((k_strided<double, 1>));
+    LSM_ATTR((k_strided_raw<double, -1>));
+    LSM_ATTR((k_fftz_green<float, false>));
+    LSM_ATTR((k_fftz_green<float, true>));
+    LSM_ATTR((k_fftz_green<double, false>));
+    LSM_ATTR((k_fftz_green<double, true>));
+    LSM_ATTR(k_fftx_out<float>);
+    LSM_ATTR(k_fftx_out<double>);
+    LSM_ATTR((k_rows<float, -1>));
+    LSM_ATTR((k_rows<float, 1>));
+    LSM_ATTR((k_rows<double, -1>));
+    LSM_ATTR((k_rows<double, 1>));
+    LSM_ATTR((k_rows_raw<double, -1>));
+#undef LSM_ATTR
+    return e;
+}
+
+}  // namespace lsm

@@ -1,0 +1,63 @@
+// common.cuh - complex helpers, grid geometry and launch bookkeeping shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lsm {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { typedef float2 type; };
+template <> struct cplx_of<double> { typedef double2 type; };
+
+template <typename C> struct real_of;
+template <> struct real_of<float2> { typedef float type; };
+template <> struct real_of<double2> { typedef double type; };
+
+template <typename C> __host__ __device__ __forceinline__ C mkc(typename real_of<C>::type re, typename real_of<C>::type im) {
+    C r; r.x = re; r.y = im; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+    C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) {
+    C r; r.x = a.x * s; r.y = a.y * s; return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { C r; r.x = a.x; r.y = -a.y; return r; }
+// multiply by (s * i), s = +1 or -1
+template <int S, typename C> __device__ __forceinline__ C cmul_si(C a) {
+    C r;
+    if (S > 0) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
+
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+template <typename C> __device__ __forceinline__ C from_d2(double2 a);
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+
+// Grid geometry of one medium.  Model nodes n_a; padded periodic length L_a = 2 n_a;
+// extended contrast-source nodes e_a = n_a + 2 (nodes -1 .. n_a).
+struct Dims {
+    int nx, ny, nz;
+    int Lx, Ly, Lz;
+    int ex, ey, ez;
+    long long N;      // nx*ny*nz
+    double h;
+};
+
+// Shared-memory FFT plan of one length.  radix[] are the Stockham stages in order.
+struct FftPlan {
+    int L;
+    int nst;
+    int radix[12];
+};
+
+}  // namespace lsm

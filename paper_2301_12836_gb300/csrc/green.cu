@@ -1,0 +1,219 @@
+// green.cu - background Green's tensor (Eq. 7, Appendix A): the sampled kernel table and the
+// moment-tensor background field (Eqs. 13-16).  All FP64.
+//
+// Both closed forms are evaluated in radial form, G_ij(x) = f(r) d_ij + g(r) g_i g_j with
+// g = x / r, so that the derivative needed by the source term is
+//   dG_ij/dx_k = f'(r) g_k d_ij + g'(r) g_i g_j g_k + g(r)/r (d_ik g_j + d_jk g_i - 2 g_i g_j g_k).
+//
+// exact (full isotropic solution, outgoing exp(+i k r)):
+//   4 pi rho f = e_b/(b^2 r) - Q,   4 pi rho g = e_a/(a^2 r) - e_b/(b^2 r) + 3 Q,
+//   Q(r) = [(1 - i k_b r) e_b - (1 - i k_a r) e_a] / (w^2 r^3) = [psi(k_b r)/b^2 - psi(k_a r)/a^2] / r,
+//   psi(x) = ((1 - i x) e^{ix} - 1) / x^2, evaluated by its Taylor series for |x| < 1/2 (no
+//   cancellation at small w r), directly otherwise; Q' = (e_b/b^2 - e_a/a^2)/r^2 - 3 Q / r.
+// paper (near field Eq. A.4 + far field Eq. A.5):
+//   4 pi rho f = e_b/(b^2 r) - 4 pi rho Cn / r,  4 pi rho g = e_a/(a^2 r) - e_b/(b^2 r) + 12 pi rho Cn / r,
+//   Cn = (1 - b^2/a^2) / (8 pi rho b^2).
+#include "kernels.h"
+
+namespace lsm {
+
+struct GreenPar {
+    double a, b, rho, w;   // P, S velocities, density, angular frequency
+    int mode;              // 0 exact, 1 paper
+};
+
+__device__ __forceinline__ double2 cexpi(double phase) {
+    double s, c;
+    sincos(phase, &s, &c);
+    return make_double2(c, s);
+}
+
+// psi(x) = ((1 - i x) e^{ix} - 1) / x^2 = sum_m i^m (m+1)/(m+2)! x^m
+__device__ __forceinline__ double2 psi(double x) {
+    if (fabs(x) < 0.5) {
+        // coefficients (m+1)/(m+2)! for m = 0..14
+        const double a[15] = {1.0 / 2.0, 2.0 / 6.0, 3.0 / 24.0, 4.0 / 120.0, 5.0 / 720.0, 6.0 / 5040.0,
+                              7.0 / 40320.0, 8.0 / 362880.0, 9.0 / 3628800.0, 10.0 / 39916800.0,
+                              11.0 / 479001600.0, 12.0 / 6227020800.0, 13.0 / 87178291200.0,
+                              14.0 / 1307674368000.0, 15.0 / 20922789888000.0};
+        // real part: m even, sign (-1)^(m/2); imaginary: m odd, sign (-1)^((m-1)/2)
+        const double x2 = x * x;
+        double re = 0.0, im = 0.0;
+        for (int m = 14; m >= 0; m -= 2) re = re * (-x2) + a[m];
+        for (int m = 13; m >= 1; m -= 2) im = im * (-x2) + a[m];
+        return make_double2(re, im * x);
+    }
+    const double2 e = cexpi(x);
+    const double x2 = x * x;
+    return make_double2((e.x + x * e.y - 1.0) / x2, (e.y - x * e.x) / x2);
+}
+
+// f, g and their radial derivatives at distance r
+__device__ void radial(const GreenPar& p, double r, double2& f, double2& g, double2& fp, double2& gp) {
+    const double c4 = 1.0 / (4.0 * M_PI * p.rho);
+    const double ka = p.w / p.a, kb = p.w / p.b;
+    const double ia2 = 1.0 / (p.a * p.a), ib2 = 1.0 / (p.b * p.b);
+    const double2 ea = cexpi(ka * r), eb = cexpi(kb * r);
+    const double ir = 1.0 / r;
+    // E_c = e_c / r and E_c' = (i k_c - 1/r) E_c
+    const double2 Ea = make_double2(ea.x * ir, ea.y * ir);
+    const double2 Eb = make_double2(eb.x * ir, eb.y * ir);
+    const double2 Eap = make_double2(-ka * Ea.y - ir * Ea.x, ka * Ea.x - ir * Ea.y);
+    const double2 Ebp = make_double2(-kb * Eb.y - ir * Eb.x, kb * Eb.x - ir * Eb.y);
+    if (p.mode == 0) {
+        const double2 pa = psi(ka * r), pb = psi(kb * r);
+        const double2 Q = make_double2((pb.x * ib2 - pa.x * ia2) * ir, (pb.y * ib2 - pa.y * ia2) * ir);
+        const double2 Qp = make_double2((eb.x * ib2 - ea.x * ia2) * ir * ir - 3.0 * Q.x * ir,
+                                        (eb.y * ib2 - ea.y * ia2) * ir * ir - 3.0 * Q.y * ir);
+        f = make_double2(c4 * (Eb.x * ib2 - Q.x), c4 * (Eb.y * ib2 - Q.y));
+        g = make_double2(c4 * (Ea.x * ia2 - Eb.x * ib2 + 3.0 * Q.x), c4 * (Ea.y * ia2 - Eb.y * ib2 + 3.0 * Q.y));
+        fp = make_double2(c4 * (Ebp.x * ib2 - Qp.x), c4 * (Ebp.y * ib2 - Qp.y));
+        gp = make_double2(c4 * (Eap.x * ia2 - Ebp.x * ib2 + 3.0 * Qp.x), c4 * (Eap.y * ia2 - Ebp.y * ib2 + 3.0 * Qp.y));
+    } else {
+        const double cn = (1.0 - p.b * p.b * ia2) / (8.0 * M_PI * p.rho) * ib2;
+        f = make_double2(c4 * Eb.x * ib2 - cn * ir, c4 * Eb.y * ib2);
+        g = make_double2(c4 * (Ea.x * ia2 - Eb.x * ib2) + 3.0 * cn * ir, c4 * (Ea.y * ia2 - Eb.y * ib2));
+        fp = make_double2(c4 * Ebp.x * ib2 + cn * ir * ir, c4 * Ebp.y * ib2);
+        gp = make_double2(c4 * (Eap.x * ia2 - Ebp.x * ib2) - 3.0 * cn * ir * ir, c4 * (Eap.y * ia2 - Ebp.y * ib2));
+    }
+}
+
+// Table on the 2n-periodic grid, [6][Lz][Ly][Lx], components (11, 22, 33, 23, 13, 12):
+// h^3 G(m h) for |m_a| <= n_a - 1, m != 0; self-cell value at m = 0; zero on planes m_a = n_a.
+__global__ void k_green_table(Dims d, GreenPar p, double2 self, double2* __restrict__ T) {
+    const long long P = (long long)d.Lx * d.Ly * d.Lz;
+    const double h3 = d.h * d.h * d.h;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % d.Lx);
+        const int iy = (int)((i / d.Lx) % d.Ly);
+        const int iz = (int)(i / ((long long)d.Lx * d.Ly));
+        double2 out[6];
+        for (int c = 0; c < 6; ++c) out[c] = make_double2(0.0, 0.0);
+        if (ix != d.nx && iy != d.ny && iz != d.nz) {
+            const int mx = ix < d.nx ? ix : ix - d.Lx;
+            const int my = iy < d.ny ? iy : iy - d.Ly;
+            const int mz = iz < d.nz ? iz : iz - d.Lz;
+            if (mx == 0 && my == 0 && mz == 0) {
+                out[0] = out[1] = out[2] = self;
+            } else {
+                const double x[3] = {mx * d.h, my * d.h, mz * d.h};
+                const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                const double gx = x[0] / r, gy = x[1] / r, gz = x[2] / r;
+                double2 f, g, fp, gp;
+                radial(p, r, f, g, fp, gp);
+                const double gg[6] = {gx * gx, gy * gy, gz * gz, gy * gz, gx * gz, gx * gy};
+                for (int c = 0; c < 6; ++c) {
+                    const double dd = c < 3 ? 1.0 : 0.0;
+                    out[c] = make_double2(h3 * (f.x * dd + g.x * gg[c]), h3 * (f.y * dd + g.y * gg[c]));
+                }
+            }
+        }
+        for (int c = 0; c < 6; ++c) T[c * P + i] = out[c];
+    }
+}
+
+// u0_i = -sum_jk M_jk dG_ij/dx_k (x - s)
+//      = -[(f' + g/r) (M g)_i + (g' - 2 g/r)(g.M g) g_i + (g/r) tr(M) g_i]
+__global__ void k_source(Dims d, GreenPar p, double M11, double M22, double M33, double M23, double M13, double M12,
+                         double sx, double sy, double sz, double2* __restrict__ u0, int* __restrict__ flag) {
+    const long long N = d.N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % d.nx);
+        const int iy = (int)((i / d.nx) % d.ny);
+        const int iz = (int)(i / ((long long)d.nx * d.ny));
+        const double x = ix * d.h - sx, y = iy * d.h - sy, z = iz * d.h - sz;
+        const double r = sqrt(x * x + y * y + z * z);
+        if (r == 0.0) {
+            for (int c = 0; c < 3; ++c) u0[c * N + i] = make_double2(0.0, 0.0);
+            atomicExch(flag, 1);
+            continue;
+        }
+        const double g[3] = {x / r, y / r, z / r};
+        double2 f, gg, fp, gp;
+        radial(p, r, f, gg, fp, gp);
+        const double Mg[3] = {M11 * g[0] + M12 * g[1] + M13 * g[2],
+                              M12 * g[0] + M22 * g[1] + M23 * g[2],
+                              M13 * g[0] + M23 * g[1] + M33 * g[2]};
+        const double gMg = g[0] * Mg[0] + g[1] * Mg[1] + g[2] * Mg[2];
+        const double tr = M11 + M22 + M33;
+        const double ir = 1.0 / r;
+        const double2 A = make_double2(fp.x + gg.x * ir, fp.y + gg.y * ir);
+        const double2 B = make_double2(gp.x - 2.0 * gg.x * ir, gp.y - 2.0 * gg.y * ir);
+        const double2 Cc = make_double2(gg.x * ir, gg.y * ir);
+        for (int c = 0; c < 3; ++c) {
+            const double s1 = Mg[c], s2 = gMg * g[c], s3 = tr * g[c];
+            u0[c * N + i] = make_double2(-(A.x * s1 + B.x * s2 + Cc.x * s3), -(A.y * s1 + B.y * s2 + Cc.y * s3));
+        }
+    }
+}
+
+static inline int gsz(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t fft3_inplace_setup(const Dims& d, const Plans& pl, double2* buf, int ncomp, cudaStream_t st, long long* nl);
+cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* oct, double scale, cudaStream_t st, long long* nl);
+
+cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, double mu, double rho, double omega,
+                               int green, double2* scratch, double2* ghat64, cudaStream_t st, long long* nl) {
+    GreenPar p;
+    p.a = sqrt((lam + 2.0 * mu) / rho);
+    p.b = sqrt(mu / rho);
+    p.rho = rho;
+    p.w = omega;
+    p.mode = green;
+    // cell average of G over [-h/2, h/2]^3 times h^3, to O(w h): the static Kelvin part gives
+    // (1/(3a^2) + 2/(3b^2)) C h^2 / (4 pi rho) with C = int_{unit cube} dV/|x| = 3 ln(2+sqrt3) - pi/2,
+    // the r^0 term of the expansion gives i w h^3 (1/(3a^3) + 2/(3b^3)) / (4 pi rho).
+    const double Cself = 3.0 * log(2.0 + sqrt(3.0)) - 0.5 * M_PI;
+    const double c4 = 1.0 / (4.0 * M_PI * rho);
+    const double h = d.h;
+    double2 self;
+    self.x = c4 * (1.0 / (3.0 * p.a * p.a) + 2.0 / (3.0 * p.b * p.b)) * Cself * h * h;
+    self.y = c4 * omega * (1.0 / (3.0 * p.a * p.a * p.a) + 2.0 / (3.0 * p.b * p.b * p.b)) * h * h * h;
+    const long long P = (long long)d.Lx * d.Ly * d.Lz;
+    k_green_table<<<gsz(P), 256, 0, st>>>(d, p, self, scratch);
+    if (nl) *nl += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = fft3_inplace_setup(d, pl64, scratch, 6, st, nl);
+    if (e != cudaSuccess) return e;
+    return launch_extract_octant(d, scratch, ghat64, 1.0 / (double)P, st, nl);
+}
+
+cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green, const double* M6,
+                          const double* xs, double2* u0, int* flag, cudaStream_t st, long long* nl) {
+    GreenPar p;
+    p.a = sqrt((lam + 2.0 * mu) / rho);
+    p.b = sqrt(mu / rho);
+    p.rho = rho;
+    p.w = omega;
+    p.mode = green;
+    k_source<<<gsz(d.N), 256, 0, st>>>(d, p, M6[0], M6[1], M6[2], M6[3], M6[4], M6[5], xs[0], xs[1], xs[2], u0, flag);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+__global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void k_f2d_c(const float2* __restrict__ in, double2* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+
+cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t st, long long* nl) {
+    k_d2f<<<gsz(n), 256, 0, st>>>(in, out, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+cudaError_t launch_f2d_c(const float2* in, double2* out, long long n, cudaStream_t st, long long* nl) {
+    k_f2d_c<<<gsz(n), 256, 0, st>>>(in, out, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace lsm

@@ -1,0 +1,64 @@
+// kernels.h - host-side launchers of the CUDA kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace lsm {
+
+// Per-system arguments of one operator application.  One entry per system of a batch;
+// kernels index them with a grid dimension.  All systems of a batch share one medium.
+template <typename T>
+struct ApplySys {
+    typedef typename cplx_of<T>::type C;
+    const C* u;          // input field [3][nz][ny][nx]
+    C* out;              // result [3][nz][ny][nx]
+    const C* ghat;       // octant Green spectrum [6][nz+1][ny+1][nx+1], scaled by 1/P
+    C* w1;               // workspace (see apply_ws_elems)
+    C* w2;               // workspace
+    T omega2;            // w^2
+    const int* run;      // system runs when run == nullptr or *run != 0
+};
+
+struct Medium {
+    Dims d;
+    const void* dC;      // [21][N] of T
+    const void* drho;    // [N] of T
+};
+
+struct Plans {
+    FftPlan px, py, pz;
+    const void* twx;     // twiddle tables of T: exp(-2 pi i k / L)
+    const void* twy;
+    const void* twz;
+};
+
+// workspace elements (complex) needed by one system's apply / adjoint, each of w1 and w2
+void apply_ws_elems(const Dims& d, long long* w1, long long* w2);
+
+// Operator A u (forward) or A^H u (adjoint) for nsys systems; sys is a device array.
+template <typename T>
+cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sys_dev, int nsys,
+                         cudaStream_t st, long long* nlaunch);
+template <typename T>
+cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* sys_dev, int nsys,
+                           cudaStream_t st, long long* nlaunch);
+
+// Green spectrum setup: writes the octant spectrum (double) scaled by 1/P into ghat64,
+// using scratch (6 * Lx*Ly*Lz complex double).  green: 0 exact, 1 paper.
+cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, double mu, double rho,
+                               double omega, int green, double2* scratch, double2* ghat64,
+                               cudaStream_t st, long long* nlaunch);
+
+// Background field u0 of a moment tensor (complex double), flag set to 1 if a node hits the source.
+cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green,
+                          const double* M6, const double* xs, double2* u0, int* flag,
+                          cudaStream_t st, long long* nlaunch);
+
+// Precision converters.
+cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t st, long long* nlaunch);
+cudaError_t launch_f2d_c(const float2* in, double2* out, long long n, cudaStream_t st, long long* nlaunch);
+
+// Dynamic shared memory opt-in for the kernels (call once per device).
+cudaError_t init_kernel_attributes();
+
+}  // namespace lsm

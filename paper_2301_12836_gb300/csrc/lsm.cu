@@ -1,0 +1,691 @@
+// lsm.cu - host side of the C ABI declared in include/lsm.h.
+//
+// Handles, device memory, FFT plans and twiddle tables, and the drivers of the BiCGSTAB solve
+// (Sec. 3.2): the plain FP64 solve and the mixed-precision solve (FP32 inner BiCGSTAB with FP64
+// inner products, FP64 outer residual and iterative refinement).  All arithmetic of the method
+// runs in the kernels of apply.cu, green.cu and solver.cu.
+#include "lsm.h"
+#include "kernels.h"
+#include "solver.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace lsm;
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr int KRY = 8;       // x, r, r^, p, v, s, t, and one scratch / inner right-hand side
+
+struct SolverWS {
+    int cap = 0;              // systems the buffers hold
+    int precision = -1;
+    long long n3 = 0;
+    void* block = nullptr;    // one allocation for everything below
+    size_t bytes = 0;
+    // device arrays
+    BcgState* st = nullptr;
+    MixState* ms = nullptr;
+    double* partials = nullptr;
+    int* n_active = nullptr;
+    void* vecs = nullptr;      // BcgVecs<T>[cap]
+    void* sys_v = nullptr;     // ApplySys<T>[cap]
+    void* sys_t = nullptr;
+    void* sys_x = nullptr;
+    ApplySys<double>* sys64 = nullptr;  // FP64 residual / true residual applies
+    void** ptrs = nullptr;     // pointer arrays for the mix kernels: 6 * cap
+    // per-system buffers (device addresses)
+    std::vector<void*> kry;    // KRY Krylov vectors per system (inner precision)
+    std::vector<void*> w1, w2; // inner-precision apply workspaces
+    std::vector<double2*> w1d, w2d, ax64;
+};
+
+struct Store {
+    int refs = 1;
+    Dims d;
+    double lam = 0, mu = 0, rho = 0;
+    int precision = LSM_FP64, green = LSM_GREEN_EXACT;
+    cudaStream_t st = nullptr;
+    double* dC64 = nullptr;
+    double* drho64 = nullptr;
+    float* dC32 = nullptr;
+    float* drho32 = nullptr;
+    Plans pl64, pl32;
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+    // single-apply workspaces and argument slots
+    double2 *w1_64 = nullptr, *w2_64 = nullptr;
+    float2 *w1_32 = nullptr, *w2_32 = nullptr;
+    ApplySys<double>* a64 = nullptr;
+    ApplySys<float>* a32 = nullptr;
+    int* flag = nullptr;
+    int* h_pinned = nullptr;   // pinned host ints for readbacks
+    SolverWS ws;
+};
+
+}  // namespace
+
+struct lsm_ctx {
+    Store* s = nullptr;
+    double omega = 0;
+    lsm_opts o;
+    double2* ghat64 = nullptr;
+    float2* ghat32 = nullptr;
+    long long nl = 0;
+    std::string err;
+};
+
+namespace {
+
+lsm_status fail(lsm_t h, lsm_status code, const std::string& msg) {
+    if (h) h->err = msg; else g_err = msg;
+    return code;
+}
+
+lsm_status cuda_fail(lsm_t h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? LSM_ERR_OOM : LSM_ERR_CUDA, m);
+}
+
+#define CK(h, call)                                          \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, #call); \
+    } while (0)
+
+bool factor_plan(int L, FftPlan& p) {
+    p.L = L;
+    p.nst = 0;
+    int m = L;
+    const int rs[5] = {8, 4, 2, 3, 5};
+    for (int k = 0; k < 5; ++k) {
+        while (m % rs[k] == 0) {
+            if (p.nst >= 12) return false;
+            p.radix[p.nst++] = rs[k];
+            m /= rs[k];
+        }
+    }
+    return m == 1;
+}
+
+// exp(-2 pi i k / L), k < L, evaluated in long double and rounded once
+void twiddle_table(int L, std::vector<double2>& t64, std::vector<float2>& t32) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = 0; k < L; ++k) {
+        const long double a = -2.0L * pi * (long double)k / (long double)L;
+        const long double c = cosl(a), s = sinl(a);
+        t64.push_back(make_double2((double)c, (double)s));
+        t32.push_back(make_float2((float)c, (float)s));
+    }
+}
+
+bool lsm_grid_ok(int n) {
+    if (n < 2 || 2 * n > 512) return false;
+    FftPlan p;
+    return factor_plan(2 * n, p);
+}
+
+void store_release(Store* s) {
+    if (!s) return;
+    if (--s->refs > 0) return;
+    cudaFree(s->dC64); cudaFree(s->drho64); cudaFree(s->dC32); cudaFree(s->drho32);
+    cudaFree(s->tw64); cudaFree(s->tw32);
+    cudaFree(s->w1_64); cudaFree(s->w2_64); cudaFree(s->w1_32); cudaFree(s->w2_32);
+    cudaFree(s->a64); cudaFree(s->a32); cudaFree(s->flag);
+    if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    cudaFree(s->ws.block);
+    delete s;
+}
+
+lsm_status ensure_apply_ws(lsm_t h) {
+    Store* s = h->s;
+    long long e1, e2;
+    apply_ws_elems(s->d, &e1, &e2);
+    if (!s->w1_64) {
+        CK(h, cudaMalloc(&s->w1_64, e1 * sizeof(double2)));
+        CK(h, cudaMalloc(&s->w2_64, e2 * sizeof(double2)));
+    }
+    if (s->precision == LSM_MIXED && !s->w1_32) {
+        CK(h, cudaMalloc(&s->w1_32, e1 * sizeof(float2)));
+        CK(h, cudaMalloc(&s->w2_32, e2 * sizeof(float2)));
+    }
+    return LSM_OK;
+}
+
+Medium medium_of(Store* s, int prec32) {
+    Medium m;
+    m.d = s->d;
+    m.dC = prec32 ? (const void*)s->dC32 : (const void*)s->dC64;
+    m.drho = prec32 ? (const void*)s->drho32 : (const void*)s->drho64;
+    return m;
+}
+
+}  // namespace
+
+extern "C" void lsm_default_opts(lsm_opts* o) {
+    if (!o) return;
+    o->precision = LSM_FP64;
+    o->green = LSM_GREEN_EXACT;
+    o->tol = 1e-10;
+    o->maxit = 1000;
+    o->inner_tol = 1e-4;
+    o->max_outer = 8;
+}
+
+static lsm_status build_spectrum(lsm_t h) {
+    Store* s = h->s;
+    const Dims& d = s->d;
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long P = (long long)d.Lx * d.Ly * d.Lz;
+    CK(h, cudaMalloc(&h->ghat64, 6 * NO * sizeof(double2)));
+    double2* scratch = nullptr;
+    CK(h, cudaMalloc(&scratch, 6 * P * sizeof(double2)));
+    cudaError_t e = launch_green_setup(d, s->pl64, s->lam, s->mu, s->rho, h->omega, s->green, scratch, h->ghat64, s->st, &h->nl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(h, e, "green spectrum setup");
+    if (s->precision == LSM_MIXED) {
+        CK(h, cudaMalloc(&h->ghat32, 6 * NO * sizeof(float2)));
+        CK(h, launch_d2f((const double*)h->ghat64, (float*)h->ghat32, 12 * NO, s->st, &h->nl));
+        CK(h, cudaStreamSynchronize(s->st));
+    }
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double lambda0, double mu0, double rho0,
+                                 const double* dC, const double* drho, double omega, const lsm_opts* opts, void* stream) {
+    if (!out) return fail(nullptr, LSM_ERR_ARG, "lsm_create: out is NULL");
+    *out = nullptr;
+    if (!n || !dC || !drho) return fail(nullptr, LSM_ERR_ARG, "lsm_create: null pointer argument");
+    for (int a = 0; a < 3; ++a)
+        if (!lsm_grid_ok(n[a]))
+            return fail(nullptr, LSM_ERR_ARG, "lsm_create: each n must be >= 2 with 2n <= 512 a product of 2, 3, 5");
+    if (!(dx > 0) || !(mu0 > 0) || !(lambda0 + 2 * mu0 > 0) || !(rho0 > 0) || !(omega > 0) || !std::isfinite(omega))
+        return fail(nullptr, LSM_ERR_ARG, "lsm_create: need dx > 0, mu0 > 0, lambda0 + 2 mu0 > 0, rho0 > 0, omega > 0");
+    lsm_opts o;
+    lsm_default_opts(&o);
+    if (opts) o = *opts;
+    if ((o.precision != LSM_FP64 && o.precision != LSM_MIXED) || (o.green != LSM_GREEN_EXACT && o.green != LSM_GREEN_PAPER) ||
+        !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1)
+        return fail(nullptr, LSM_ERR_ARG, "lsm_create: invalid options");
+    static bool attrs_done = false;
+    if (!attrs_done) {
+        cudaError_t e = init_kernel_attributes();
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "kernel attributes");
+        attrs_done = true;
+    }
+    lsm_t h = new lsm_ctx();
+    h->o = o;
+    h->omega = omega;
+    Store* s = new Store();
+    h->s = s;
+    s->st = (cudaStream_t)stream;
+    s->precision = o.precision;
+    s->green = o.green;
+    s->lam = lambda0; s->mu = mu0; s->rho = rho0;
+    Dims& d = s->d;
+    d.nx = n[0]; d.ny = n[1]; d.nz = n[2];
+    d.Lx = 2 * d.nx; d.Ly = 2 * d.ny; d.Lz = 2 * d.nz;
+    d.ex = d.nx + 2; d.ey = d.ny + 2; d.ez = d.nz + 2;
+    d.N = (long long)d.nx * d.ny * d.nz;
+    d.h = dx;
+    lsm_status rc = LSM_OK;
+    auto bail = [&](lsm_status r) { g_err = h->err; lsm_destroy(h); return r; };
+#define CKB(call)                                                    \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return bail(cuda_fail(h, _e, #call)); \
+    } while (0)
+    // plans + twiddles
+    {
+        factor_plan(d.Lx, s->pl64.px); factor_plan(d.Ly, s->pl64.py); factor_plan(d.Lz, s->pl64.pz);
+        s->pl32.px = s->pl64.px; s->pl32.py = s->pl64.py; s->pl32.pz = s->pl64.pz;
+        std::vector<double2> t64;
+        std::vector<float2> t32;
+        twiddle_table(d.Lx, t64, t32);
+        twiddle_table(d.Ly, t64, t32);
+        twiddle_table(d.Lz, t64, t32);
+        CKB(cudaMalloc(&s->tw64, t64.size() * sizeof(double2)));
+        CKB(cudaMalloc(&s->tw32, t32.size() * sizeof(float2)));
+        CKB(cudaMemcpy(s->tw64, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        CKB(cudaMemcpy(s->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        s->pl64.twx = s->tw64; s->pl64.twy = s->tw64 + d.Lx; s->pl64.twz = s->tw64 + d.Lx + d.Ly;
+        s->pl32.twx = s->tw32; s->pl32.twy = s->tw32 + d.Lx; s->pl32.twz = s->tw32 + d.Lx + d.Ly;
+    }
+    // contrast copies
+    CKB(cudaMalloc(&s->dC64, 21 * d.N * sizeof(double)));
+    CKB(cudaMalloc(&s->drho64, d.N * sizeof(double)));
+    CKB(cudaMemcpyAsync(s->dC64, dC, 21 * d.N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CKB(cudaMemcpyAsync(s->drho64, drho, d.N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    if (o.precision == LSM_MIXED) {
+        CKB(cudaMalloc(&s->dC32, 21 * d.N * sizeof(float)));
+        CKB(cudaMalloc(&s->drho32, d.N * sizeof(float)));
+        CKB(launch_d2f(s->dC64, s->dC32, 21 * d.N, s->st, &h->nl));
+        CKB(launch_d2f(s->drho64, s->drho32, d.N, s->st, &h->nl));
+    }
+    CKB(cudaMalloc(&s->a64, sizeof(ApplySys<double>)));
+    CKB(cudaMalloc(&s->a32, sizeof(ApplySys<float>)));
+    CKB(cudaMalloc(&s->flag, sizeof(int)));
+    CKB(cudaMallocHost(&s->h_pinned, 16 * sizeof(int)));
+    rc = build_spectrum(h);
+    if (rc != LSM_OK) return bail(rc);
+#undef CKB
+    *out = h;
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_create_shared(lsm_t* out, lsm_t base, double omega) {
+    if (!out) return fail(nullptr, LSM_ERR_ARG, "lsm_create_shared: out is NULL");
+    *out = nullptr;
+    if (!base) return fail(nullptr, LSM_ERR_ARG, "lsm_create_shared: base is NULL");
+    if (!(omega > 0) || !std::isfinite(omega)) return fail(nullptr, LSM_ERR_ARG, "lsm_create_shared: omega must be > 0");
+    lsm_t h = new lsm_ctx();
+    h->o = base->o;
+    h->omega = omega;
+    h->s = base->s;
+    h->s->refs++;
+    lsm_status rc = build_spectrum(h);
+    if (rc != LSM_OK) {
+        g_err = h->err;
+        lsm_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return LSM_OK;
+}
+
+extern "C" void lsm_destroy(lsm_t h) {
+    if (!h) return;
+    cudaFree(h->ghat64);
+    cudaFree(h->ghat32);
+    store_release(h->s);
+    delete h;
+}
+
+extern "C" const char* lsm_last_error(lsm_t h) {
+    if (h) return h->err.c_str();
+    return g_err.c_str();
+}
+
+extern "C" long long lsm_launch_count(lsm_t h) { return h ? h->nl : 0; }
+
+extern "C" lsm_status lsm_source(lsm_t h, const double M[6], const double xs[3], void* u0) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_source: null handle");
+    if (!M || !xs || !u0) return fail(h, LSM_ERR_ARG, "lsm_source: null pointer argument");
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(M[k])) return fail(h, LSM_ERR_ARG, "lsm_source: moment tensor not finite");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(xs[k])) return fail(h, LSM_ERR_ARG, "lsm_source: source position not finite");
+    Store* s = h->s;
+    CK(h, cudaMemsetAsync(s->flag, 0, sizeof(int), s->st));
+    CK(h, launch_source(s->d, s->lam, s->mu, s->rho, h->omega, s->green, M, xs, (double2*)u0, s->flag, s->st, &h->nl));
+    CK(h, cudaMemcpyAsync(s->h_pinned, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(h, cudaStreamSynchronize(s->st));
+    if (s->h_pinned[0]) {
+        h->err = "lsm_source: a grid node coincides with the source; u0 set to 0 there";
+        return LSM_WARN_SOURCE_ON_NODE;
+    }
+    return LSM_OK;
+}
+
+template <typename T>
+static lsm_status apply_one(lsm_t h, const void* u, void* Au, bool adjoint) {
+    typedef typename cplx_of<T>::type C;
+    Store* s = h->s;
+    lsm_status rc = ensure_apply_ws(h);
+    if (rc != LSM_OK) return rc;
+    const bool f32 = sizeof(T) == 4;
+    ApplySys<T> a;
+    a.u = (const C*)u;
+    a.out = (C*)Au;
+    a.ghat = f32 ? (const C*)h->ghat32 : (const C*)h->ghat64;
+    a.w1 = f32 ? (C*)s->w1_32 : (C*)s->w1_64;
+    a.w2 = f32 ? (C*)s->w2_32 : (C*)s->w2_64;
+    a.omega2 = (T)(h->omega * h->omega);
+    a.run = nullptr;
+    ApplySys<T>* dev = f32 ? (ApplySys<T>*)s->a32 : (ApplySys<T>*)s->a64;
+    CK(h, cudaMemcpyAsync(dev, &a, sizeof(a), cudaMemcpyHostToDevice, s->st));
+    const Plans& pl = f32 ? s->pl32 : s->pl64;
+    Medium m = medium_of(s, f32);
+    cudaError_t e = adjoint ? launch_adjoint<T>(m, pl, dev, 1, s->st, &h->nl) : launch_apply<T>(m, pl, dev, 1, s->st, &h->nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, adjoint ? "adjoint" : "apply");
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_apply(lsm_t h, const void* u, void* Au) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_apply: null handle");
+    if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply: u and Au must be distinct non-null device buffers");
+    return apply_one<double>(h, u, Au, false);
+}
+
+extern "C" lsm_status lsm_apply_c64(lsm_t h, const void* u, void* Au) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_apply_c64: null handle");
+    if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply_c64: u and Au must be distinct non-null device buffers");
+    if (h->s->precision != LSM_MIXED) return fail(h, LSM_ERR_ARG, "lsm_apply_c64: handle was not created with LSM_MIXED");
+    return apply_one<float>(h, u, Au, false);
+}
+
+extern "C" lsm_status lsm_adjoint(lsm_t h, const void* v, void* AHv) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_adjoint: null handle");
+    if (!v || !AHv || v == AHv) return fail(h, LSM_ERR_ARG, "lsm_adjoint: v and AHv must be distinct non-null device buffers");
+    return apply_one<double>(h, v, AHv, true);
+}
+
+// ---------------------------------------------------------------------------------------------
+// solver workspace
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+lsm_status ensure_solver_ws(lsm_t h, int nsys) {
+    Store* s = h->s;
+    SolverWS& w = s->ws;
+    const long long n3 = 3 * s->d.N;
+    if (w.cap >= nsys && w.precision == s->precision) return LSM_OK;
+    cudaFree(w.block);
+    w = SolverWS();
+    long long e1, e2;
+    apply_ws_elems(s->d, &e1, &e2);
+    const bool mixed = s->precision == LSM_MIXED;
+    const size_t csz = mixed ? sizeof(float2) : sizeof(double2);
+    const int nblk = vec_blocks(n3);
+    // layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+    const size_t o_st = take(nsys * sizeof(BcgState));
+    const size_t o_ms = take(nsys * sizeof(MixState));
+    const size_t o_pt = take((size_t)nsys * nblk * 4 * sizeof(double));
+    const size_t o_na = take(sizeof(int));
+    const size_t o_vecs = take(nsys * sizeof(BcgVecs<double>));
+    const size_t o_sv = take(nsys * sizeof(ApplySys<double>));
+    const size_t o_stt = take(nsys * sizeof(ApplySys<double>));
+    const size_t o_sx = take(nsys * sizeof(ApplySys<double>));
+    const size_t o_s64 = take(nsys * sizeof(ApplySys<double>));
+    const size_t o_ptr = take(6 * (size_t)nsys * sizeof(void*));
+    std::vector<size_t> o_kry, o_w1, o_w2, o_w1d, o_w2d, o_ax;
+    for (int i = 0; i < nsys; ++i) {
+        for (int k = 0; k < KRY; ++k) o_kry.push_back(take(n3 * csz));
+        if (mixed) {
+            // FP64 residual-apply workspaces; the FP32 inner ones alias their first halves
+            // (the FP64 apply and the inner solve never run at the same time)
+            o_w1d.push_back(take(e1 * sizeof(double2)));
+            o_w2d.push_back(take(e2 * sizeof(double2)));
+            o_ax.push_back(take(n3 * sizeof(double2)));
+        } else {
+            o_w1.push_back(take(e1 * csz));
+            o_w2.push_back(take(e2 * csz));
+        }
+    }
+    w.bytes = off;
+    cudaError_t e = cudaMalloc(&w.block, off);
+    if (e != cudaSuccess) {
+        w = SolverWS();
+        return cuda_fail(h, e, "solver workspace");
+    }
+    char* b = (char*)w.block;
+    w.cap = nsys;
+    w.precision = s->precision;
+    w.n3 = n3;
+    w.st = (BcgState*)(b + o_st);
+    w.ms = (MixState*)(b + o_ms);
+    w.partials = (double*)(b + o_pt);
+    w.n_active = (int*)(b + o_na);
+    w.vecs = b + o_vecs;
+    w.sys_v = b + o_sv;
+    w.sys_t = b + o_stt;
+    w.sys_x = b + o_sx;
+    w.sys64 = (ApplySys<double>*)(b + o_s64);
+    w.ptrs = (void**)(b + o_ptr);
+    for (int i = 0; i < nsys; ++i) {
+        for (int k = 0; k < KRY; ++k) w.kry.push_back(b + o_kry[i * KRY + k]);
+        if (mixed) {
+            w.w1d.push_back((double2*)(b + o_w1d[i]));
+            w.w2d.push_back((double2*)(b + o_w2d[i]));
+            w.w1.push_back(b + o_w1d[i]);
+            w.w2.push_back(b + o_w2d[i]);
+            w.ax64.push_back((double2*)(b + o_ax[i]));
+        } else {
+            w.w1.push_back(b + o_w1[i]);
+            w.w2.push_back(b + o_w2[i]);
+        }
+    }
+    return LSM_OK;
+}
+
+// Run BiCGSTAB on nsys systems whose vectors/apply arguments are already on the device.
+template <typename T>
+lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, double tol, int maxit, bool x_zero,
+                        const MixState* skip, std::vector<BcgState>& out) {
+    Store* s = h0->s;
+    SolverWS& w = s->ws;
+    const long long n3 = w.n3;
+    const cudaStream_t st = s->st;
+    Partials pt;
+    pt.buf = w.partials;
+    pt.nblk = vec_blocks(n3);
+    BcgVecs<T>* vecs = (BcgVecs<T>*)w.vecs;
+    ApplySys<T>* sv = (ApplySys<T>*)w.sys_v;
+    ApplySys<T>* stt = (ApplySys<T>*)w.sys_t;
+    ApplySys<T>* sx = (ApplySys<T>*)w.sys_x;
+    const bool f32 = sizeof(T) == 4;
+    const Plans& pl = f32 ? s->pl32 : s->pl64;
+    Medium m = medium_of(s, f32);
+    long long* nl = &h0->nl;
+    std::vector<BcgState> init(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        BcgState& b = init[i];
+        memset(&b, 0, sizeof(b));
+        b.tol2 = tol * tol;
+        b.maxit = maxit;
+        b.active = 0;
+    }
+    CK(h0, cudaMemcpyAsync(w.st, init.data(), nsys * sizeof(BcgState), cudaMemcpyHostToDevice, st));
+    CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
+    if (!x_zero) {
+        cudaError_t e = launch_apply<T>(m, pl, sx, nsys, st, nl);
+        if (e != cudaSuccess) return cuda_fail(h0, e, "initial residual apply");
+    }
+    CK(h0, bcg_init<T>(vecs, w.st, pt, n3, nsys, x_zero ? 1 : 0, skip, w.n_active, st, nl));
+    CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h0, cudaStreamSynchronize(st));
+    int n_active = s->h_pinned[0];
+    int guard = 0;
+    while (n_active > 0 && guard++ <= maxit + 1) {
+        CK(h0, bcg_update_p<T>(vecs, w.st, n3, nsys, pt.nblk, st, nl));
+        cudaError_t e = launch_apply<T>(m, pl, sv, nsys, st, nl);
+        if (e != cudaSuccess) return cuda_fail(h0, e, "apply p");
+        CK(h0, bcg_alpha<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
+        CK(h0, bcg_s<T>(vecs, w.st, pt, n3, nsys, st, nl));
+        e = launch_apply<T>(m, pl, stt, nsys, st, nl);
+        if (e != cudaSuccess) return cuda_fail(h0, e, "apply s");
+        CK(h0, bcg_omega<T>(vecs, w.st, pt, n3, nsys, st, nl));
+        CK(h0, bcg_xr<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
+        CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(h0, cudaStreamSynchronize(st));
+        n_active = s->h_pinned[0];
+    }
+    out.resize(nsys);
+    CK(h0, cudaMemcpyAsync(out.data(), w.st, nsys * sizeof(BcgState), cudaMemcpyDeviceToHost, st));
+    CK(h0, cudaStreamSynchronize(st));
+    return LSM_OK;
+}
+
+}  // namespace
+
+extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void* const* b, void* const* x, int* iters,
+                                        double* relres, lsm_status* status) {
+    if (nsys < 1 || !hs_in || !b || !x) return fail(nullptr, LSM_ERR_ARG, "lsm_solve_batched: bad arguments");
+    std::vector<lsm_t> hs(hs_in, hs_in + nsys);
+    for (int i = 0; i < nsys; ++i) {
+        if (!hs[i]) return fail(nullptr, LSM_ERR_ARG, "lsm_solve_batched: null handle");
+        if (hs[i]->s != hs[0]->s) return fail(hs[0], LSM_ERR_ARG, "lsm_solve_batched: handles must share one medium");
+        if (!b[i] || !x[i] || b[i] == x[i]) return fail(hs[0], LSM_ERR_ARG, "lsm_solve_batched: b and x must be distinct device buffers");
+    }
+    lsm_t h0 = hs[0];
+    Store* s = h0->s;
+    const cudaStream_t st = s->st;
+    lsm_status rc = ensure_solver_ws(h0, nsys);
+    if (rc != LSM_OK) return rc;
+    SolverWS& w = s->ws;
+    const long long n3 = w.n3;
+    const bool mixed = s->precision == LSM_MIXED;
+    const double tol = h0->o.tol;
+    Partials pt;
+    pt.buf = w.partials;
+    pt.nblk = vec_blocks(n3);
+    std::vector<int> it_out(nsys, 0);
+    std::vector<double> rr_out(nsys, 0.0);
+    std::vector<lsm_status> stat(nsys, LSM_OK);
+    // final-residual / FP64 apply arguments
+    std::vector<ApplySys<double>> a64(nsys);
+    std::vector<MixState> ms(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        memset(&ms[i], 0, sizeof(MixState));
+        ms[i].tol = tol;
+    }
+    if (!mixed) {
+        std::vector<BcgVecs<double>> V(nsys);
+        std::vector<ApplySys<double>> sv(nsys), stt(nsys), sx(nsys);
+        for (int i = 0; i < nsys; ++i) {
+            double2** k = (double2**)&w.kry[i * KRY];
+            V[i].b = (const double2*)b[i];
+            V[i].x = (double2*)x[i];
+            V[i].r = k[0]; V[i].rh = k[1]; V[i].p = k[2]; V[i].v = k[3]; V[i].s = k[4]; V[i].t = k[5];
+            ApplySys<double> a;
+            a.ghat = hs[i]->ghat64;
+            a.w1 = (double2*)w.w1[i];
+            a.w2 = (double2*)w.w2[i];
+            a.omega2 = hs[i]->omega * hs[i]->omega;
+            a.u = V[i].p; a.out = V[i].v; a.run = &w.st[i].run_v; sv[i] = a;
+            a.u = V[i].s; a.out = V[i].t; a.run = &w.st[i].run_t; stt[i] = a;
+            a.u = V[i].x; a.out = V[i].v; a.run = nullptr; sx[i] = a;
+            a.u = V[i].x; a.out = k[6]; a.run = nullptr; a64[i] = a;   // true residual at exit
+        }
+        CK(h0, cudaMemcpyAsync(w.vecs, V.data(), nsys * sizeof(V[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys_v, sv.data(), nsys * sizeof(sv[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys_t, stt.data(), nsys * sizeof(stt[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys_x, sx.data(), nsys * sizeof(sx[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys64, a64.data(), nsys * sizeof(a64[0]), cudaMemcpyHostToDevice, st));
+        std::vector<BcgState> fin;
+        rc = run_bicgstab<double>(h0, hs, nsys, tol, h0->o.maxit, false, nullptr, fin);
+        if (rc != LSM_OK) return rc;
+        for (int i = 0; i < nsys; ++i) {
+            it_out[i] = fin[i].iters;
+            stat[i] = (lsm_status)fin[i].status;
+            // b = 0: the solution is exactly zero whatever the initial guess
+            if (fin[i].bnorm2 == 0.0) CK(h0, cudaMemsetAsync(x[i], 0, n3 * sizeof(double2), st));
+        }
+        // true residual ||b - A x|| / ||b|| (Eq. 22)
+        Medium m = medium_of(s, 0);
+        cudaError_t e = launch_apply<double>(m, s->pl64, w.sys64, nsys, st, &h0->nl);
+        if (e != cudaSuccess) return cuda_fail(h0, e, "final residual apply");
+        void** P = w.ptrs;
+        std::vector<void*> hp(6 * nsys);
+        for (int i = 0; i < nsys; ++i) {
+            hp[i] = const_cast<void*>(b[i]);
+            hp[nsys + i] = w.kry[i * KRY + 6];
+            hp[2 * nsys + i] = w.kry[i * KRY + 7];   // residual scratch
+        }
+        CK(h0, cudaMemcpyAsync(P, hp.data(), 6 * nsys * sizeof(void*), cudaMemcpyHostToDevice, st));
+        ms.assign(nsys, MixState());
+        for (int i = 0; i < nsys; ++i) { memset(&ms[i], 0, sizeof(MixState)); ms[i].tol = 0.0; }
+        CK(h0, cudaMemcpyAsync(w.ms, ms.data(), nsys * sizeof(MixState), cudaMemcpyHostToDevice, st));
+        CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms, pt,
+                            n3, nsys, w.n_active, st, &h0->nl));
+        CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
+        CK(h0, cudaStreamSynchronize(st));
+        for (int i = 0; i < nsys; ++i) rr_out[i] = ms[i].relres;
+    } else {
+        // mixed precision: FP64 outer residual + FP32 inner BiCGSTAB on the normalised residual
+        std::vector<BcgVecs<float>> V(nsys);
+        std::vector<ApplySys<float>> sv(nsys), stt(nsys);
+        for (int i = 0; i < nsys; ++i) {
+            float2** k = (float2**)&w.kry[i * KRY];
+            V[i].x = k[0];   // correction d
+            V[i].r = k[1]; V[i].rh = k[2]; V[i].p = k[3]; V[i].v = k[4]; V[i].s = k[5]; V[i].t = k[6];
+            V[i].b = k[7];   // normalised FP32 residual
+            ApplySys<float> a;
+            a.ghat = hs[i]->ghat32;
+            a.w1 = (float2*)w.w1[i];
+            a.w2 = (float2*)w.w2[i];
+            a.omega2 = (float)(hs[i]->omega * hs[i]->omega);
+            a.u = V[i].p; a.out = V[i].v; a.run = &w.st[i].run_v; sv[i] = a;
+            a.u = V[i].s; a.out = V[i].t; a.run = &w.st[i].run_t; stt[i] = a;
+            ApplySys<double> d;
+            d.ghat = hs[i]->ghat64;
+            d.w1 = w.w1d[i];
+            d.w2 = w.w2d[i];
+            d.omega2 = hs[i]->omega * hs[i]->omega;
+            d.u = (const double2*)x[i];
+            d.out = w.ax64[i];
+            d.run = &w.ms[i].run;
+            a64[i] = d;
+        }
+        CK(h0, cudaMemcpyAsync(w.vecs, V.data(), nsys * sizeof(V[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys_v, sv.data(), nsys * sizeof(sv[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys_t, stt.data(), nsys * sizeof(stt[0]), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(w.sys64, a64.data(), nsys * sizeof(a64[0]), cudaMemcpyHostToDevice, st));
+        void** P = w.ptrs;
+        std::vector<void*> hp(6 * nsys);
+        for (int i = 0; i < nsys; ++i) {
+            hp[i] = const_cast<void*>(b[i]);
+            hp[nsys + i] = w.ax64[i];
+            hp[2 * nsys + i] = w.ax64[i];     // r64 overwrites ax64 in place
+            hp[3 * nsys + i] = w.kry[i * KRY + 7];  // r32 (inner b)
+            hp[4 * nsys + i] = x[i];
+            hp[5 * nsys + i] = w.kry[i * KRY + 0];  // d32
+        }
+        CK(h0, cudaMemcpyAsync(P, hp.data(), 6 * nsys * sizeof(void*), cudaMemcpyHostToDevice, st));
+        for (int i = 0; i < nsys; ++i) ms[i].run = 1;
+        CK(h0, cudaMemcpyAsync(w.ms, ms.data(), nsys * sizeof(MixState), cudaMemcpyHostToDevice, st));
+        Medium m64 = medium_of(s, 0);
+        const int nblk = pt.nblk;
+        for (int outer = 0;; ++outer) {
+            cudaError_t e = launch_apply<double>(m64, s->pl64, w.sys64, nsys, st, &h0->nl);
+            if (e != cudaSuccess) return cuda_fail(h0, e, "FP64 residual apply");
+            CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
+            CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms,
+                                pt, n3, nsys, w.n_active, st, &h0->nl));
+            CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(h0, cudaStreamSynchronize(st));
+            if (s->h_pinned[0] == 0 || outer >= h0->o.max_outer) break;
+            CK(h0, mix_down((double2* const*)(P + 2 * nsys), (float2* const*)(P + 3 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
+            for (int i = 0; i < nsys; ++i) CK(h0, cudaMemsetAsync(w.kry[i * KRY + 0], 0, n3 * sizeof(float2), st));
+            std::vector<BcgState> fin;
+            rc = run_bicgstab<float>(h0, hs, nsys, h0->o.inner_tol, h0->o.maxit, true, w.ms, fin);
+            if (rc != LSM_OK) return rc;
+            for (int i = 0; i < nsys; ++i) it_out[i] += fin[i].iters;
+            CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
+        }
+        CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
+        CK(h0, cudaStreamSynchronize(st));
+        for (int i = 0; i < nsys; ++i) {
+            rr_out[i] = ms[i].relres;
+            stat[i] = ms[i].done ? LSM_OK : LSM_ERR_NOCONV;
+            if (ms[i].bnorm2 == 0.0) CK(h0, cudaMemsetAsync(x[i], 0, n3 * sizeof(double2), st));
+        }
+        CK(h0, cudaStreamSynchronize(st));
+    }
+    lsm_status first = LSM_OK;
+    for (int i = 0; i < nsys; ++i) {
+        if (iters) iters[i] = it_out[i];
+        if (relres) relres[i] = rr_out[i];
+        if (status) status[i] = stat[i];
+        if (stat[i] != LSM_OK && first == LSM_OK) first = stat[i];
+    }
+    if (first != LSM_OK) h0->err = first == LSM_ERR_NOCONV ? "solve: iteration limit reached" : "solve: BiCGSTAB breakdown";
+    return first;
+}
+
+extern "C" lsm_status lsm_solve(lsm_t h, const void* b, void* x, int* iters, double* relres) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_solve: null handle");
+    const void* bb[1] = {b};
+    void* xx[1] = {x};
+    return lsm_solve_batched(1, &h, bb, xx, iters, relres, nullptr);
+}

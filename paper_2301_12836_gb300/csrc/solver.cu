@@ -1,0 +1,418 @@
+// solver.cu - BiCGSTAB vector updates, FP64 inner products and the mixed-precision refinement
+// kernels (Sec. 3.2, Eq. 22).
+//
+// Every reduction is two-stage and deterministic: each CTA reduces its slice with warp shuffles
+// and writes one partial; the last CTA to finish (atomic ticket after a memory fence) sums the
+// partials in block order and updates the system's scalars on the device.  Kernels of systems
+// that stopped return at once, so a batch keeps launching one grid per step whatever its mix of
+// converged and running systems.
+#include "solver.cuh"
+
+namespace lsm {
+
+static constexpr int VTH = 256;
+
+int vec_blocks(long long n) {
+    long long b = (n + VTH * 4 - 1) / (VTH * 4);
+    if (b > 2 * 152) b = 2 * 152;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[wid * K + k] = v[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = lane < nw ? sh[lane * K + k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            v[k] = a;
+        }
+    }
+}
+
+// Reduce v over the grid's x dimension for system sys.  Returns true in thread 0 of the last
+// CTA, with tot holding the system's sums.
+template <int K>
+__device__ __forceinline__ bool grid_sum(double (&v)[K], Partials pt, int sys, unsigned int* counter, double (&tot)[K]) {
+    __shared__ double sh[32 * K];
+    __shared__ int last;
+    block_sum<K>(v, sh);
+    if (threadIdx.x == 0) {
+        double* dst = pt.buf + ((long long)sys * pt.nblk + blockIdx.x) * 4;
+#pragma unroll
+        for (int k = 0; k < K; ++k) dst[k] = v[k];
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double a[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double* src = pt.buf + ((long long)sys * pt.nblk + b) * 4;
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] += __ldcg(&src[k]);
+    }
+    block_sum<K>(a, sh);
+    if (threadIdx.x == 0) {
+        *counter = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] = a[k];
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// conj(a) b accumulated in FP64
+template <typename C>
+__device__ __forceinline__ void acc_dot(double& re, double& im, C a, C b) {
+    const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+    re += ax * bx + ay * by;
+    im += ax * by - ay * bx;
+}
+template <typename C>
+__device__ __forceinline__ void acc_nrm(double& s, C a) {
+    const double ax = a.x, ay = a.y;
+    s += ax * ax + ay * ay;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VTH) k_bcg_init(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
+                                                  Partials pt, long long n, int x_zero, const MixState* __restrict__ skip,
+                                                  int* n_active) {
+    typedef typename cplx_of<T>::type C;
+    const int sys = blockIdx.y;
+    if (skip && skip[sys].done) return;
+    const BcgVecs<T> V = vecs[sys];
+    double v[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const C b = V.b[i];
+        C r = b;
+        if (!x_zero) r = csub(b, V.v[i]);
+        V.r[i] = r;
+        V.rh[i] = r;
+        acc_nrm(v[0], b);
+        acc_nrm(v[1], r);
+    }
+    double tot[2];
+    if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
+        BcgState& S = st[sys];
+        S.bnorm2 = tot[0];
+        S.rnorm2 = tot[1];
+        S.rho = make_double2(tot[1], 0.0);
+        S.tol2 = S.tol2 * tot[0];
+        S.iters = 0;
+        S.half = 0;
+        S.status = 0;
+        S.active = (tot[0] > 0.0 && tot[1] > S.tol2) ? 1 : 0;
+        S.run_v = S.run_t = S.active;
+        if (S.active) atomicAdd(n_active, 1);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VTH) k_bcg_p(const BcgVecs<T>* __restrict__ vecs, const BcgState* __restrict__ st, long long n) {
+    typedef typename cplx_of<T>::type C;
+    const int sys = blockIdx.y;
+    const BcgState& S = st[sys];
+    if (!S.active) return;
+    const BcgVecs<T> V = vecs[sys];
+    if (S.iters == 0) {
+        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) V.p[i] = V.r[i];
+        return;
+    }
+    const C be = from_d2<C>(S.beta), om = from_d2<C>(S.omega);
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const C pv = csub(V.p[i], cmul(om, V.v[i]));
+        V.p[i] = cadd(V.r[i], cmul(be, pv));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VTH) k_bcg_alpha(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
+                                                   Partials pt, long long n, int* n_active) {
+    typedef typename cplx_of<T>::type C;
+    const int sys = blockIdx.y;
+    if (!st[sys].run_v) return;
+    const BcgVecs<T> V = vecs[sys];
+    double v[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH)
+        acc_dot(v[0], v[1], V.rh[i], V.v[i]);
+    double tot[2];
+    if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
+        BcgState& S = st[sys];
+        S.rv = make_double2(tot[0], tot[1]);
+        const double2 a = cdiv(S.rho, S.rv);
+        if ((tot[0] == 0.0 && tot[1] == 0.0) || !finite2(a)) {
+            S.status = -4;
+            S.active = S.run_v = S.run_t = 0;
+            atomicSub(n_active, 1);
+        } else {
+            S.alpha = a;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VTH) k_bcg_s(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
+                                               Partials pt, long long n) {
+    typedef typename cplx_of<T>::type C;
+    const int sys = blockIdx.y;
+    if (!st[sys].active) return;
+    const BcgVecs<T> V = vecs[sys];
+    const C al = from_d2<C>(st[sys].alpha);
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const C s = csub(V.r[i], cmul(al, V.v[i]));
+        V.s[i] = s;
+        acc_nrm(v[0], s);
+    }
+    double tot[1];
+    if (grid_sum<1>(v, pt, sys, &st[sys].counter, tot)) {
+        BcgState& S = st[sys];
+        S.snorm2 = tot[0];
+        if (tot[0] <= S.tol2) {
+            S.half = 1;
+            S.run_t = 0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VTH) k_bcg_omega(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
+                                                   Partials pt, long long n) {
+    typedef typename cplx_of<T>::type C;
+    const int sys = blockIdx.y;
+    if (!st[sys].run_t) return;
+    const BcgVecs<T> V = vecs[sys];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const C t = V.t[i];
+        acc_dot(v[0], v[1], t, V.s[i]);
+        acc_nrm(v[2], t);
+    }
+    double tot[3];
+    if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) {
+        BcgState& S = st[sys];
+        S.ts = make_double2(tot[0], tot[1]);
+        S.tt = tot[2];
+        // a zero <t,t> is caught as a breakdown by k_bcg_xr (omega = 0 there)
+        S.omega = tot[2] > 0.0 ? make_double2(tot[0] / tot[2], tot[1] / tot[2]) : make_double2(0.0, 0.0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
+                                                Partials pt, long long n, int* n_active) {
+    typedef typename cplx_of<T>::type C;
+    const int sys = blockIdx.y;
+    if (!st[sys].active) return;
+    const BcgVecs<T> V = vecs[sys];
+    const int half = st[sys].half;
+    const C al = from_d2<C>(st[sys].alpha);
+    const C om = from_d2<C>(st[sys].omega);
+    double v[3] = {0.0, 0.0, 0.0};
+    if (half) {
+        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH)
+            V.x[i] = cadd(V.x[i], cmul(al, V.p[i]));
+    } else {
+        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+            const C s = V.s[i], t = V.t[i];
+            V.x[i] = cadd(V.x[i], cadd(cmul(al, V.p[i]), cmul(om, s)));
+            const C r = csub(s, cmul(om, t));
+            V.r[i] = r;
+            acc_nrm(v[0], r);
+            acc_dot(v[1], v[2], V.rh[i], r);
+        }
+    }
+    double tot[3];
+    if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) {
+        BcgState& S = st[sys];
+        S.iters += 1;
+        if (half) {
+            S.rnorm2 = S.snorm2;
+            S.active = 0;
+            S.status = 0;
+        } else {
+            S.rnorm2 = tot[0];
+            const double2 rho_new = make_double2(tot[1], tot[2]);
+            if (tot[0] <= S.tol2) {
+                S.active = 0;
+                S.status = 0;
+            } else if ((S.omega.x == 0.0 && S.omega.y == 0.0) || (rho_new.x == 0.0 && rho_new.y == 0.0) ||
+                       !finite2(rho_new) || !isfinite(tot[0])) {
+                S.active = 0;
+                S.status = -4;
+            } else if (S.iters >= S.maxit) {
+                S.active = 0;
+                S.status = -5;
+            } else {
+                S.beta = cmuld(cdiv(rho_new, S.rho), cdiv(S.alpha, S.omega));
+                S.rho = rho_new;
+            }
+        }
+        S.half = 0;
+        S.run_v = S.run_t = S.active;
+        if (!S.active) atomicSub(n_active, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// mixed-precision refinement
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restrict__ b, const double2* const* __restrict__ ax,
+                                                 double2* const* __restrict__ r64, MixState* __restrict__ ms, Partials pt,
+                                                 long long n, int* n_active) {
+    const int sys = blockIdx.y;
+    if (ms[sys].done) return;
+    const double2* B = b[sys];
+    const double2* AX = ax[sys];
+    double2* R = r64[sys];
+    double v[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const double2 bb = B[i], a = AX[i];
+        const double2 r = make_double2(bb.x - a.x, bb.y - a.y);
+        R[i] = r;
+        v[0] += bb.x * bb.x + bb.y * bb.y;
+        v[1] += r.x * r.x + r.y * r.y;
+    }
+    double tot[2];
+    if (grid_sum<2>(v, pt, sys, &ms[sys].counter, tot)) {
+        MixState& M = ms[sys];
+        M.bnorm2 = tot[0];
+        M.rnorm2 = tot[1];
+        M.relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+        M.done = (M.relres <= M.tol || tot[1] == 0.0) ? 1 : 0;
+        M.run = !M.done;
+        if (!M.done) atomicAdd(n_active, 1);
+    }
+}
+
+__global__ void __launch_bounds__(VTH) k_mix_down(double2* const* __restrict__ r64, float2* const* __restrict__ r32,
+                                                  const MixState* __restrict__ ms, long long n) {
+    const int sys = blockIdx.y;
+    if (ms[sys].done) return;
+    const double sc = 1.0 / sqrt(ms[sys].rnorm2);
+    const double2* R = r64[sys];
+    float2* D = r32[sys];
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const double2 r = R[i];
+        D[i] = make_float2((float)(r.x * sc), (float)(r.y * sc));
+    }
+}
+
+__global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64, float2* const* __restrict__ d32,
+                                                const MixState* __restrict__ ms, long long n) {
+    const int sys = blockIdx.y;
+    if (ms[sys].done) return;
+    const double sc = sqrt(ms[sys].rnorm2);
+    double2* X = x64[sys];
+    const float2* D = d32[sys];
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const float2 d = D[i];
+        double2 x = X[i];
+        x.x += sc * (double)d.x;
+        x.y += sc * (double)d.y;
+        X[i] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t bcg_init(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int x_zero,
+                     const MixState* skip, int* n_active, cudaStream_t s, long long* nl) {
+    k_bcg_init<T><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(vecs, st, pt, n, x_zero, skip, n_active);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t bcg_update_p(const BcgVecs<T>* vecs, BcgState* st, long long n, int nsys, int nblk, cudaStream_t s, long long* nl) {
+    k_bcg_p<T><<<dim3(nblk, nsys), VTH, 0, s>>>(vecs, st, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t bcg_alpha(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int* n_active, cudaStream_t s,
+                      long long* nl) {
+    k_bcg_alpha<T><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(vecs, st, pt, n, n_active);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t bcg_s(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl) {
+    k_bcg_s<T><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(vecs, st, pt, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t bcg_omega(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl) {
+    k_bcg_omega<T><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(vecs, st, pt, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int* n_active, cudaStream_t s,
+                   long long* nl) {
+    k_bcg_xr<T><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(vecs, st, pt, n, n_active);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+#define LSM_INST(T)                                                                                                   \
+    template cudaError_t bcg_init<T>(const BcgVecs<T>*, BcgState*, Partials, long long, int, int, const MixState*,   \
+                                     int*, cudaStream_t, long long*);                                                 \
+    template cudaError_t bcg_update_p<T>(const BcgVecs<T>*, BcgState*, long long, int, int, cudaStream_t, long long*); \
+    template cudaError_t bcg_alpha<T>(const BcgVecs<T>*, BcgState*, Partials, long long, int, int*, cudaStream_t,     \
+                                      long long*);                                                                    \
+    template cudaError_t bcg_s<T>(const BcgVecs<T>*, BcgState*, Partials, long long, int, cudaStream_t, long long*);  \
+    template cudaError_t bcg_omega<T>(const BcgVecs<T>*, BcgState*, Partials, long long, int, cudaStream_t, long long*); \
+    template cudaError_t bcg_xr<T>(const BcgVecs<T>*, BcgState*, Partials, long long, int, int*, cudaStream_t, long long*);
+LSM_INST(float)
+LSM_INST(double)
+#undef LSM_INST
+
+cudaError_t mix_residual(const double2* const* b, const double2* const* ax, double2* const* r64, MixState* ms, Partials pt,
+                         long long n, int nsys, int* n_active, cudaStream_t s, long long* nl) {
+    k_mix_res<<<dim3(pt.nblk, nsys), VTH, 0, s>>>(b, ax, r64, ms, pt, n, n_active);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms, long long n, int nsys, int nblk, cudaStream_t s,
+                     long long* nl) {
+    k_mix_down<<<dim3(nblk, nsys), VTH, 0, s>>>(r64, r32, ms, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+cudaError_t mix_up(double2* const* x64, float2* const* d32, const MixState* ms, long long n, int nsys, int nblk, cudaStream_t s,
+                   long long* nl) {
+    k_mix_up<<<dim3(nblk, nsys), VTH, 0, s>>>(x64, d32, ms, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace lsm

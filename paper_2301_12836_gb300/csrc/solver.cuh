@@ -1,0 +1,80 @@
+// solver.cuh - BiCGSTAB state and launchers (internal).
+#pragma once
+#include "kernels.h"
+
+namespace lsm {
+
+// Device-resident state of one system's BiCGSTAB (Sec. 3.2; Van der Vorst 1992).  Scalars in FP64.
+struct BcgState {
+    double2 rho;        // <r^, r> of the current iteration
+    double2 alpha;
+    double2 omega;
+    double2 beta;       // for the next p update
+    double2 rv;         // <r^, v>
+    double2 ts;         // <t, s>
+    double tt;          // <t, t>
+    double bnorm2;      // ||b||^2
+    double tol2;        // (tol ||b||)^2
+    double rnorm2;      // ||r||^2 of the last update
+    double snorm2;
+    int iters;
+    int maxit;
+    int status;         // 0 ok / running, <0 lsm_status error
+    int active;         // still iterating
+    int half;           // converged on the half step this iteration
+    int run_v;          // apply p -> v runs
+    int run_t;          // apply s -> t runs
+    unsigned int counter;
+};
+
+template <typename T>
+struct BcgVecs {
+    typedef typename cplx_of<T>::type C;
+    const C* b;
+    C *x, *r, *rh, *p, *v, *s, *t;
+};
+
+// Refinement state of one system in the mixed-precision solve (FP64 outer residual).
+struct MixState {
+    double bnorm2;
+    double rnorm2;
+    double relres;
+    double tol;
+    int done;
+    int run;            // FP64 residual apply runs
+    unsigned int counter;
+};
+
+struct Partials {
+    double* buf;        // [nsys][nblk][4]
+    int nblk;
+};
+
+// skip: optional per-system refinement state; systems with skip[i].done keep the state the host wrote
+template <typename T>
+cudaError_t bcg_init(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int x_zero,
+                     const MixState* skip, int* n_active, cudaStream_t s, long long* nl);
+template <typename T>
+cudaError_t bcg_update_p(const BcgVecs<T>* vecs, BcgState* st, long long n, int nsys, int nblk, cudaStream_t s, long long* nl);
+template <typename T>
+cudaError_t bcg_alpha(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int* n_active,
+                      cudaStream_t s, long long* nl);
+template <typename T>
+cudaError_t bcg_s(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl);
+template <typename T>
+cudaError_t bcg_omega(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl);
+template <typename T>
+cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int* n_active,
+                   cudaStream_t s, long long* nl);
+
+// mixed refinement: r64 = b - ax (relres), r32 = r64/||r64||, x64 += ||r64|| d32
+cudaError_t mix_residual(const double2* const* b, const double2* const* ax, double2* const* r64, MixState* ms,
+                         Partials pt, long long n, int nsys, int* n_active, cudaStream_t s, long long* nl);
+cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms, long long n, int nsys, int nblk,
+                     cudaStream_t s, long long* nl);
+cudaError_t mix_up(double2* const* x64, float2* const* d32, const MixState* ms, long long n, int nsys, int nblk,
+                   cudaStream_t s, long long* nl);
+
+int vec_blocks(long long n);
+
+}  // namespace lsm

@@ -1,0 +1,197 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 unless stated):
+* FP64 apply / adjoint / source: 1e-12.  Both sides evaluate the same sums in
+  FP64; FFT rounding grows like u log2(P) ~ 1e-15 * 20, well below 1e-12.
+* FP32 apply: 1e-5.  FP32 FFTs and contraction carry ~6e-8 * log2(P) relative
+  error on the scattered part, a fraction of the field.
+* FP64 solve: 1e-10 with both sides solved to relres 1e-12 (cond(A) is O(10)).
+* mixed solve: 1e-6 with the mixed solve taken to relres 1e-8.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as sy
+from oracle import operator as op, solver as osv, source as osrc
+from paper_2301_12836_gb300 import lsm
+
+from gpu_helpers import dev, field, handle, host, rel
+
+pytestmark = pytest.mark.gpu
+
+W = 2 * np.pi * 10.0
+
+
+def _oracle_apply(med, omega, u, mode="exact"):
+    return op.FFTOperator(med, omega, mode).apply(u)
+
+
+@pytest.mark.parametrize("mode,green", [("exact", lsm.LSM_GREEN_EXACT), ("paper", lsm.LSM_GREEN_PAPER)])
+def test_source_parity(mode, green):
+    med = sy.random_medium((9, 7, 11), h=10.0, seed=21)
+    h = handle(med, W, green=green)
+    xs = np.array([41.3, 27.9, 55.2])
+    M = np.array([0.3, -1.2, 0.7, 0.25, -0.4, 0.9])
+    u0 = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    code = lsm.lsm_source(h, M, xs, u0)
+    assert code == lsm.LSM_OK
+    want, hit = osrc.background_field(med.n, med.h, M, xs, W, med.lam0, med.mu0, med.rho0, mode)
+    assert not hit
+    assert rel(host(u0).reshape(want.shape), want) < 1e-12
+
+
+def test_source_on_node_flag():
+    med = sy.random_medium((6, 6, 6), h=10.0, seed=22)
+    h = handle(med, W)
+    u0 = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    code = lsm.lsm_source(h, sy.explosion(), [20.0, 30.0, 40.0], u0)
+    assert code == lsm.LSM_WARN_SOURCE_ON_NODE
+    got = host(u0).reshape(3, 6, 6, 6)
+    assert np.all(got[:, 4, 3, 2] == 0)
+    want, hit = osrc.background_field(med.n, med.h, sy.explosion(), np.array([20.0, 30.0, 40.0]), W,
+                                      med.lam0, med.mu0, med.rho0)
+    assert hit and rel(got, want) < 1e-12
+
+
+# grids spanning several tiles in every pass, ragged tails, odd and non-cubic sizes, minimum size
+GRIDS = [(2, 2, 2), (5, 3, 4), (20, 18, 15), (16, 16, 16), (12, 25, 9)]
+
+
+@pytest.mark.parametrize("n", GRIDS)
+@pytest.mark.parametrize("mode,green", [("exact", lsm.LSM_GREEN_EXACT), ("paper", lsm.LSM_GREEN_PAPER)])
+def test_apply_fp64_parity(n, mode, green):
+    med = sy.random_medium(n, h=8.0, seed=sum(n), frac=0.2)
+    h = handle(med, W, green=green)
+    u = field(med.shape, 1)
+    Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_apply(h, dev(u).reshape(-1), Au)
+    want = _oracle_apply(med, W, u, mode)
+    assert rel(host(Au).reshape(u.shape), want) < 1e-12
+    assert rel(u, want) > 1e-3  # the scattered part is resolved
+
+
+@pytest.mark.parametrize("n", [(20, 18, 15), (16, 16, 16)])
+def test_apply_fp32_parity(n):
+    med = sy.random_medium(n, h=8.0, seed=3, frac=0.2)
+    h = handle(med, W, precision=lsm.LSM_MIXED)
+    u = field(med.shape, 2)
+    Au = torch.empty(3 * h.N, dtype=torch.complex64, device="cuda")
+    lsm.lsm_apply_c64(h, dev(u, torch.complex64).reshape(-1), Au)
+    want = _oracle_apply(med, W, u)
+    assert rel(host(Au).reshape(u.shape).astype(np.complex128), want) < 1e-5
+
+
+@pytest.mark.parametrize("n", [(5, 3, 4), (20, 18, 15)])
+def test_adjoint_parity(n):
+    med = sy.random_medium(n, h=8.0, seed=5, frac=0.2)
+    h = handle(med, W)
+    w = field(med.shape, 3)
+    out = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_adjoint(h, dev(w).reshape(-1), out)
+    want = op.FFTOperator(med, W).adjoint(w)
+    assert rel(host(out).reshape(w.shape), want) < 1e-12
+    # dot-product test through the GPU alone: <A v, w> = <v, A^H w>
+    v = field(med.shape, 4)
+    Av = torch.empty_like(out)
+    lsm.lsm_apply(h, dev(v).reshape(-1), Av)
+    lhs = np.vdot(w.reshape(-1), host(Av))
+    rhs = np.vdot(v.reshape(-1), host(out))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-12
+
+
+def test_zero_contrast_is_identity_bitwise():
+    med = sy.random_medium((12, 10, 9), seed=6)
+    med.dC[:] = 0
+    med.drho[:] = 0
+    h = handle(med, W, precision=lsm.LSM_MIXED)
+    u = dev(field(med.shape, 5)).reshape(-1)
+    Au = torch.empty_like(u)
+    lsm.lsm_apply(h, u, Au)
+    assert torch.equal(Au, u)
+    u32 = u.to(torch.complex64)
+    A32 = torch.empty_like(u32)
+    lsm.lsm_apply_c64(h, u32, A32)
+    assert torch.equal(A32, u32)
+
+
+def test_solve_fp64_inclusion16():
+    """16^3 VTI cube inclusion, explosion at the centre, 10 Hz, FP64 solve vs the oracle's BiCGSTAB."""
+    wl = sy.get_workload("inclusion16_fp64")
+    med = wl.medium()
+    M, xs = wl.sources()
+    w = 2 * np.pi * wl.freqs_hz[0]
+    h = handle(med, w, tol=1e-12)
+    b = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    assert lsm.lsm_source(h, M[0], xs[0], b) == lsm.LSM_OK
+    x = torch.zeros_like(b)
+    code, it, rr = lsm.lsm_solve(h, b, x)
+    assert code == lsm.LSM_OK and rr <= 1e-12
+    u0, _ = osrc.background_field(med.n, med.h, M[0], xs[0], w, med.lam0, med.mu0, med.rho0)
+    xo, ito, rro, sto, _ = osv.bicgstab(op.FFTOperator(med, w).apply, u0, tol=1e-12, maxit=200)
+    assert sto == 0
+    assert rel(host(x).reshape(u0.shape), xo) < 1e-10
+    assert abs(it - ito) <= 1
+
+
+def test_solve_mixed_layers():
+    """Three VTI layers (the 64^3 workload's medium at 24^3), strike-slip source, mixed solve to 1e-8."""
+    med = sy.layered_vti_medium(24, 10.0)
+    w = 2 * np.pi * 15.0
+    h = handle(med, w, precision=lsm.LSM_MIXED, tol=1e-8)
+    xs = np.array([115.0, 115.0, 120.0])
+    b = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_source(h, sy.double_couple_12(), xs, b)
+    x = torch.zeros_like(b)
+    code, it, rr = lsm.lsm_solve(h, b, x)
+    assert code == lsm.LSM_OK and rr <= 1e-8
+    u0, _ = osrc.background_field(med.n, med.h, sy.double_couple_12(), xs, w, med.lam0, med.mu0, med.rho0)
+    F = op.FFTOperator(med, w)
+    xo, *_ = osv.bicgstab(F.apply, u0, tol=1e-12, maxit=400)
+    assert rel(host(x).reshape(u0.shape), xo) < 1e-6
+    # the reported residual is the true FP64 one (Eq. 22)
+    assert abs(osv.relres(F.apply, u0, host(x).reshape(u0.shape)) - rr) < 1e-9
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(lsm.LSM_FP64, 1e-11, 1e-9), (lsm.LSM_MIXED, 1e-8, 1e-6)])
+def test_solve_batched_frequencies_and_sources(precision, tol, bar):
+    """2 frequencies x 2 sources in one batched solve, each system against the oracle."""
+    med = sy.random_medium((10, 12, 9), h=10.0, seed=7, frac=0.1)
+    ws = [2 * np.pi * 6.0, 2 * np.pi * 14.0]
+    h0 = handle(med, ws[0], precision=precision, tol=tol)
+    h1 = lsm.lsm_create_shared(h0, ws[1])
+    srcs = [(sy.explosion(), np.array([44.0, 51.0, 37.0])), (sy.double_couple_13(), np.array([31.0, 62.0, 45.0]))]
+    hs, bs, xs, want = [], [], [], []
+    for hh, w in ((h0, ws[0]), (h1, ws[1])):
+        for M, s in srcs:
+            b = torch.empty(3 * hh.N, dtype=torch.complex128, device="cuda")
+            lsm.lsm_source(hh, M, s, b)
+            hs.append(hh)
+            bs.append(b)
+            xs.append(torch.zeros_like(b))
+            u0, _ = osrc.background_field(med.n, med.h, M, s, w, med.lam0, med.mu0, med.rho0)
+            xo, *_ = osv.bicgstab(op.FFTOperator(med, w).apply, u0, tol=1e-13, maxit=400)
+            want.append(xo)
+    code, its, rrs, sts = lsm.lsm_solve_batched(hs, bs, xs)
+    assert code == lsm.LSM_OK and all(s == 0 for s in sts)
+    for x, xo, rr in zip(xs, want, rrs):
+        assert rr <= tol
+        assert rel(host(x).reshape(xo.shape), xo) < bar
+
+
+def test_solve_zero_rhs_and_noconv():
+    med = sy.random_medium((8, 8, 8), h=10.0, seed=8, frac=0.1)
+    h = handle(med, W, maxit=1, tol=1e-14)
+    b = torch.zeros(3 * h.N, dtype=torch.complex128, device="cuda")
+    x = dev(field(med.shape, 9)).reshape(-1)
+    code, it, rr = lsm.lsm_solve(h, b, x, check=False)
+    assert code == lsm.LSM_OK and it == 0
+    assert torch.count_nonzero(x).item() == 0   # b = 0 gives x = 0 whatever the guess
+    # one iteration cannot reach 1e-14: NOCONV with the last iterate returned
+    lsm.lsm_source(h, sy.explosion(), [35.0, 35.0, 35.0], b)
+    x.zero_()
+    code, it, rr = lsm.lsm_solve(h, b, x, check=False)
+    assert code == lsm.LSM_ERR_NOCONV and it == 1
+    u0 = host(b).reshape(3, 8, 8, 8)
+    rr_o = osv.relres(op.FFTOperator(med, W).apply, u0, host(x).reshape(u0.shape))
+    assert abs(rr_o - rr) < 1e-12 and rr < 1.0
