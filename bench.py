@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-free elastic Lippmann-Schwinger solve on GB300.
+
+Workload (default "grf128_batched"): 128^3 grid, dx = 8 m, isotropic background
+(vp 3000, vs 1730 m/s, rho 2300 kg/m^3) plus a seeded Gaussian-random-field
+orthorhombic contrast (5% std, 40 m correlation; all 21 stiffness entries
+stored and processed), 32 frequencies 2-40 Hz x 8 random unit-norm moment
+tensors at the centre.  One step = the hot path for one frequency: the 8
+moment-tensor background fields (Eqs. 13-16) and one batched mixed-precision
+BiCGSTAB solve of the 8 systems (FP32 applies, FP64 inner products, FP64
+residual and refinement) to relative residual 1e-6.  Consecutive steps take
+consecutive frequencies.  The Green spectrum of each frequency is built before
+timing (it is set up once per frequency and shared by all its sources).
+
+value = LS operator applications (system-level matvecs, FP32 + FP64) per second
+over the whole job; solves/s is reported beside it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LS matvecs/s and solves/s at 128³ (FP32+refine vs FP64), % of HBM roofline"
+STAGES = {0: "k_stress", 1: "k_div_fftx", 2: "k_strided(y fwd)", 3: "k_fftz_green", 4: "k_strided(y inv)", 5: "k_fftx_out"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grf128_batched")
+    ap.add_argument("--grid", type=int, default=None, help="override the grid size (small profiling cases)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--systems", type=int, default=8, help="moment tensors solved together per step")
+    ap.add_argument("--timer-stage", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------------
+# algorithmic bytes of each apply stage, per system apply (b: bytes per complex, c: per real)
+# --------------------------------------------------------------------------------------------
+def stage_bytes(stage, n, b, c):
+    nx, ny, nz = n
+    N = nx * ny * nz
+    Lx, Ly = 2 * nx, 2 * ny
+    ex, ey, ez = nx + 2, ny + 2, nz + 2
+    NO = (nx + 1) * (ny + 1) * (nz + 1)
+    del ex
+    return {
+        0: (3 * b + 21 * c + 6 * b) * N,
+        1: 9 * N * b + N * c + 3 * ez * ey * Lx * b,
+        2: 3 * ez * ey * Lx * b + 3 * ez * Ly * Lx * b,
+        3: 3 * ez * Ly * Lx * b + 6 * NO * b + 3 * nz * Ly * Lx * b,
+        4: 3 * nz * Ly * Lx * b + 3 * nz * ny * Lx * b,
+        5: 3 * nz * ny * Lx * b + 3 * N * b + 3 * N * b,
+    }[stage]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profile(stage, precision, n):
+    """DRAM bytes per system apply of the timed stage from the committed ncu summary, if it matches."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want_src = _csrc_digest()
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    try:
+        if (int(rec["stage"]) != stage or rec["precision"] != precision or rec["csrc_sha256"] != want_src):
+            return None
+        scale = (n[0] * n[1] * n[2]) / float(rec["grid_voxels"])
+        return float(rec["dram_bytes_per_system_apply"]) * scale
+    except (KeyError, ValueError):
+        return None
+
+
+def _csrc_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2301_12836_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, one operator apply of the same workload
+# --------------------------------------------------------------------------------------------
+def oracle_apply_sample(med, omega, reps=1):
+    from oracle import operator as op
+    t0 = time.perf_counter()
+    F = op.FFTOperator(med, omega)
+    setup = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((3,) + med.shape) + 1j * rng.standard_normal((3,) + med.shape)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        F.apply(u)
+        times.append(time.perf_counter() - t0)
+    return setup, times
+
+
+def workload_inputs(args):
+    import synthetic as sy
+    wl = sy.get_workload(args.workload)
+    n = args.grid or wl.n
+    if args.grid:
+        med = sy.grf_orthorhombic_medium(n, wl.h) if args.workload.startswith("grf") else sy.random_medium(n, wl.h)
+    else:
+        med = wl.medium()
+    M, xs = wl.sources()
+    c = (n - 1) / 2.0 * wl.h
+    if args.grid:
+        xs = np.repeat(np.array([[c, c, c]]), len(M), axis=0)
+    k = min(args.systems, len(M))
+    if k < args.systems:
+        rng = np.random.default_rng(sy.BASE_SEED + 77)
+        M = np.concatenate([M, sy.random_moment_tensors(args.systems - k, rng)])
+        xs = np.repeat(xs[:1], args.systems, axis=0)
+    return wl, med, M[:args.systems], xs[:args.systems]
+
+
+def run_reference(args, rank, world):
+    """The oracle, timed on the host cores: each step one LS apply of the workload."""
+    if rank != 0:
+        return
+    wl, med, M, xs = workload_inputs(args)
+    omega = 2 * np.pi * wl.freqs_hz[0]
+    setup, times = oracle_apply_sample(med, omega, reps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    T = sum(timed)
+    value = len(timed) / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(timed), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args, wl, med),
+        "cpu_baseline": {"value": value, "unit": "matvec/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one FP64 NumPy FFT apply of the {med.n[0]}^3 workload per step "
+                                   f"(operator setup {setup:.1f} s untimed)"},
+        "e2e": {"value": value, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, wl, med):
+    f = wl.freqs_hz
+    return {"workload": wl.name if not args.grid else f"{wl.name}@{args.grid}", "grid": list(med.n), "dx_m": med.h,
+            "frequencies_hz": f"{f[0]:g}-{f[-1]:g} ({len(f)})", "systems_per_step": args.systems,
+            "precision": args.precision, "tol": wl.tol, "parallelism": "replicas",
+            "l2": "inputs larger than L2 (contrast, Green spectra and Krylov vectors exceed 126 MB)"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2301_12836_gb300 import lsm
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lsm.load()
+    wl, med, M, xs = workload_inputs(args)
+    nsys = args.systems
+    prec = lsm.LSM_MIXED if args.precision == "mixed" else lsm.LSM_FP64
+    steps_total = args.warmup + args.steps
+    freqs = list(wl.freqs_hz)
+    # weak scaling: rank r takes its own frequencies
+    fidx = [(rank * steps_total + s) % len(freqs) for s in range(steps_total)]
+    dC = torch.from_numpy(med.dC).cuda().contiguous()
+    drho = torch.from_numpy(med.drho).cuda().contiguous()
+    opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000)
+    handles = {}
+    t_setup = time.perf_counter()
+    base = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[0]], opts)
+    handles[fidx[0]] = base
+    for i in fidx:
+        if i not in handles:
+            handles[i] = lsm.lsm_create_shared(base, 2 * np.pi * freqs[i])
+    del dC, drho
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    N3 = 3 * base.N
+    b = [torch.empty(N3, dtype=torch.complex128, device="cuda") for _ in range(nsys)]
+    x = [torch.zeros(N3, dtype=torch.complex128, device="cuda") for _ in range(nsys)]
+    stats = {"iters": [], "relres": []}
+
+    def step(s, host_out=None):
+        h = handles[fidx[s]]
+        for j in range(nsys):
+            lsm.lsm_source(h, M[j], xs[j], b[j])
+            x[j].zero_()
+        code, its, rrs, sts = lsm.lsm_solve_batched([h] * nsys, b, x, check=False)
+        if code != lsm.LSM_OK:
+            raise RuntimeError(f"solve failed: {lsm.STATUS_NAMES.get(code)} {sts} relres {rrs}")
+        stats["iters"].extend(its)
+        stats["relres"].extend(rrs)
+        if host_out is not None:
+            for j in range(nsys):
+                host_out[j].copy_(x[j], non_blocking=True)
+
+    for s in range(args.warmup):
+        step(s)
+    stats = {"iters": [], "relres": []}
+    launches0 = sum(lsm.lsm_launch_count(h) for h in handles.values())
+    lsm.lsm_timer_start(base, args.timer_stage, prec)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(args.warmup, steps_total):
+            step(s)
+        e1.record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t_ms, t_launch, a64, a32 = lsm.lsm_timer_read(base)
+    launches = sum(lsm.lsm_launch_count(h) for h in handles.values()) - launches0
+    solves = args.steps * nsys
+    applies = a64 + a32
+    tot = torch.tensor([ms, applies, solves, launches], dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = tot[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot[1:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, applies_all, solves_all, launches_all = float(mx[0]), *[float(v) for v in sm]
+    else:
+        ms_max, applies_all, solves_all, launches_all = ms, float(applies), float(solves), float(launches)
+    value = applies_all / (ms_max / 1e3)
+    # roofline of the timed stage (FP32 applies in the mixed form, FP64 in the plain one)
+    bsz, csz = (8, 4) if prec == lsm.LSM_MIXED else (16, 8)
+    napp = a32 if prec == lsm.LSM_MIXED else a64
+    per_app = stage_bytes(args.timer_stage, med.n, bsz, csz)
+    peak, peak_kind = peaks()
+    achieved = per_app * napp / (t_ms / 1e3) / 1e9 if t_ms > 0 else 0.0
+    traffic = traffic_from_profile(args.timer_stage, args.precision, med.n)
+    roof = {"bound": "hbm", "kernel": STAGES[args.timer_stage] + ("<float>" if prec == lsm.LSM_MIXED else "<double>"),
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_system_apply": per_app,
+            "timed_launches": t_launch, "timed_ms": round(t_ms, 3),
+            "share_of_step": round(t_ms / ms, 4) if ms > 0 else None}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "matvec/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == lsm.LSM_MIXED else "f64",
+        "data": "synthetic", "config": _config(args, wl, med),
+        "solves_per_s": round(solves_all / (ms_max / 1e3), 4),
+        "matvecs": {"fp32": a32, "fp64": a64, "per_solve": round(applies / solves, 2)},
+        "iterations_mean": round(float(np.mean(stats["iters"])), 2),
+        "relres_max": float(np.max(stats["relres"])),
+        "setup_s": round(t_setup, 2),
+        "roofline": roof, "gpu_launches": int(launches_all),
+    }
+    cs = sampler.summary()
+    if cs:
+        line["clocks"] = cs
+
+    # end to end through the C ABI with host buffers: results copied to pinned host memory each step
+    if not args.no_e2e:
+        host = [torch.empty(N3, dtype=torch.complex128, pin_memory=True) for _ in range(nsys)]
+        lsm.lsm_timer_start(base, -1, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(args.warmup, steps_total):
+            step(s, host_out=host)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        _, _, e64, e32 = lsm.lsm_timer_read(base)
+        line["e2e"] = {"value": round((e64 + e32) / te, 3), "unit": "matvec/s",
+                       "h2d_bytes_per_step": nsys * 9 * 8, "d2h_bytes_per_step": nsys * N3 * 16,
+                       "solves_per_s": round(solves / te, 4)}
+
+    # the plain FP64 GPU form on the first frequency, for the precision comparison
+    if prec == lsm.LSM_MIXED and not args.no_fp64_form and rank == 0:
+        dC = torch.from_numpy(med.dC).cuda().contiguous()
+        drho = torch.from_numpy(med.drho).cuda().contiguous()
+        o64 = lsm.lsm_default_opts(precision=lsm.LSM_FP64, tol=wl.tol, maxit=2000)
+        h64 = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[-1]], o64)
+        del dC, drho
+        for j in range(nsys):
+            lsm.lsm_source(h64, M[j], xs[j], b[j])
+            x[j].zero_()
+        lsm.lsm_timer_start(h64, -1, lsm.LSM_FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code, its, rrs, sts = lsm.lsm_solve_batched([h64] * nsys, b, x, check=False)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        _, _, f64, _ = lsm.lsm_timer_read(h64)
+        line["fp64_form"] = {"solves_per_s": round(nsys / tf, 4), "matvecs_per_s": round(f64 / tf, 3),
+                             "iterations_mean": float(np.mean(its)), "relres_max": float(np.max(rrs)),
+                             "status": lsm.STATUS_NAMES.get(code), "frequency_hz": freqs[fidx[-1]]}
+        del h64
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        setup, times = oracle_apply_sample(med, 2 * np.pi * freqs[fidx[0]], reps=1)
+        line["cpu_baseline"] = {"value": round(1.0 / times[0], 5), "unit": "matvec/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 NumPy FFT apply of the {med.n[0]}^3 workload "
+                                          f"({times[0]:.1f} s; operator setup {setup:.1f} s untimed)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -81,7 +81,7 @@ void lsm_default_opts(lsm_opts *o);
  *
  *   out      host pointer receiving the handle (set to NULL on failure)
  *   n        host int[3] = {nx, ny, nz}; each n_a >= 2 and 2 n_a must factor into
- *            2, 3 and 5 with 2 n_a <= 1024
+ *            2, 3 and 5 with 2 n_a <= 512
  *   dx       grid spacing [m], > 0
  *   lambda0, mu0, rho0  background Lame parameters [Pa] and density [kg/m^3], mu0 > 0,
  *            lambda0 + 2 mu0 > 0, rho0 > 0
@@ -170,6 +170,23 @@ lsm_status lsm_solve_batched(int nsys, const lsm_t *hs, const void *const *b, vo
 
 /* Number of kernel launches the library has issued on this handle (diagnostics). */
 long long lsm_launch_count(lsm_t h);
+
+/*
+ * Diagnostics for roofline measurement (no counterpart in the paper).
+ * lsm_timer_start: from now on, record a CUDA event pair around every launch of
+ * one stage of the operator apply, on the handle's stream, for applies in the
+ * given precision (LSM_FP64, or LSM_MIXED for the FP32 applies), on every
+ * handle that shares h's medium; also zero the executed-apply counters.
+ * Stages: 0 strain + contraction, 1 contrast source + x FFT, 2 y FFT,
+ * 3 z FFT + Green multiply + inverse z FFT, 4 inverse y FFT,
+ * 5 inverse x FFT + epilogue; -1 times nothing.  Synchronises the stream.
+ * lsm_timer_read: synchronise, then report the total milliseconds and launches
+ * of the timed stage, and the number of system-level operator applies executed
+ * in FP64 and FP32 since lsm_timer_start (systems masked out of a batched
+ * launch are not counted).  Any out-pointer may be NULL.
+ */
+lsm_status lsm_timer_start(lsm_t h, int stage, int precision);
+lsm_status lsm_timer_read(lsm_t h, double *ms, long long *launches, long long *applies64, long long *applies32);
 
 /* Release every device buffer the handle owns (shared contrast when its last user goes). */
 void lsm_destroy(lsm_t h);

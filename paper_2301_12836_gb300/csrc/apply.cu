@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(NTH) k_fftx_out(Dims d, const ApplySys<T>* __r
             S.out[idx] = csub(S.u[idx], r[(x + 1) * LD + l]);
         }
     }
+    if (S.count && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(S.count, 1ull);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -567,13 +568,19 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
     const C* twx = (const C*)pl.twx;
     const C* twy = (const C*)pl.twy;
     const C* twz = (const C*)pl.twz;
+    KTimer* tm = m.timer;
+    const bool f32 = sizeof(T) == 4;
     // 1. strain + contraction
+    ktimer_mark(tm, 0, f32, st, 0);
     k_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
+    ktimer_mark(tm, 0, f32, st, 1);
     // 2. contrast source + forward x FFT -> w2 [3][ez][ey][Lx]
     {
         const int B = rows_per_tile<T>(d.Lx);
         const size_t sm = 2 * (size_t)d.Lx * (3 * B + 1) * sizeof(C);
+        ktimer_mark(tm, 1, f32, st, 0);
         k_div_fftx<T><<<dim3(cdiv(d.ey, B), d.ez, nsys), NTH, sm, st>>>(d, drho, sys, pl.px, twx, B);
+        ktimer_mark(tm, 1, f32, st, 1);
     }
     // 3. forward y FFT: w2 [3][ez][ey][Lx] -> w1 [3][ez][Ly][Lx]
     {
@@ -584,13 +591,17 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
         a.dst_es = d.Lx; a.dst_os1 = (long long)d.Ly * d.Lx; a.dst_os2 = (long long)d.ez * d.Ly * d.Lx;
         a.ncomp = 3; a.src_sel = 3; a.dst_sel = 2;
         const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        ktimer_mark(tm, 2, f32, st, 0);
         k_strided<T, -1><<<dim3(cdiv(d.Lx, a.TX), d.ez, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
+        ktimer_mark(tm, 2, f32, st, 1);
     }
     // 4. z FFT, Green multiply, inverse z FFT, crop: w1 [3][ez][Ly][Lx] -> w2 [3][nz][Ly][Lx]
     {
         const int TX = strided_tx<T>(d.Lz, 3);
         const size_t sm = 2 * (size_t)d.Lz * 3 * TX * sizeof(C);
+        ktimer_mark(tm, 3, f32, st, 0);
         k_fftz_green<T, false><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), NTH, sm, st>>>(d, pl.pz, twz, sys, TX, d.ez, 0, d.nz, 1, 2, 3);
+        ktimer_mark(tm, 3, f32, st, 1);
     }
     // 5. inverse y FFT + crop: w2 [3][nz][Ly][Lx] -> w1 [3][nz][ny][Lx]
     {
@@ -601,13 +612,17 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
         a.dst_es = d.Lx; a.dst_os1 = (long long)d.ny * d.Lx; a.dst_os2 = (long long)d.nz * d.ny * d.Lx;
         a.ncomp = 3; a.src_sel = 3; a.dst_sel = 2;
         const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        ktimer_mark(tm, 4, f32, st, 0);
         k_strided<T, 1><<<dim3(cdiv(d.Lx, a.TX), d.nz, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
+        ktimer_mark(tm, 4, f32, st, 1);
     }
     // 6. inverse x FFT + crop + Au = u - u_s
     {
         const int B = rows_per_tile<T>(d.Lx);
         const size_t sm = 2 * (size_t)d.Lx * (3 * B + 1) * sizeof(C);
+        ktimer_mark(tm, 5, f32, st, 0);
         k_fftx_out<T><<<dim3(cdiv(d.ny, B), d.nz, nsys), NTH, sm, st>>>(d, sys, pl.px, twx, B);
+        ktimer_mark(tm, 5, f32, st, 1);
     }
     if (nl) *nl += 6;
     return cudaGetLastError();
@@ -735,6 +750,32 @@ cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* o
     k_extract_octant<<<grid_elems(6 * NO), NTH, 0, st>>>(d, full, oct, scale);
     if (nl) *nl += 1;
     return cudaGetLastError();
+}
+
+void ktimer_mark(KTimer* t, int stage, bool f32, cudaStream_t st, int end) {
+    if (!t || t->stage != stage || t->f32 != (int)f32 || !t->ev) return;
+    if (!end) {
+        if (t->used >= t->cap) return;
+        cudaEventRecord(t->ev[2 * t->used], st);
+        t->open = 1;
+    } else if (t->open) {
+        cudaEventRecord(t->ev[2 * t->used + 1], st);
+        t->used++;
+        t->open = 0;
+    }
+}
+
+// Add the recorded pairs to the totals (the caller has synchronised the stream).
+void ktimer_flush(KTimer* t) {
+    if (!t || !t->ev) return;
+    for (int i = 0; i < t->used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t->ev[2 * i], t->ev[2 * i + 1]) == cudaSuccess) {
+            t->ms += ms;
+            t->launches++;
+        }
+    }
+    t->used = 0;
 }
 
 cudaError_t init_kernel_attributes() {

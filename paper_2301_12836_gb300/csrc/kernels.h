@@ -17,12 +17,29 @@ struct ApplySys {
     C* w2;               // workspace
     T omega2;            // w^2
     const int* run;      // system runs when run == nullptr or *run != 0
+    unsigned long long* count;  // incremented once per executed system apply (may be nullptr)
 };
+
+// CUDA-event timing of one stage of the apply (diagnostics).  Stages: 0 stress, 1 div+fftx,
+// 2 fft y forward, 3 fft z + Green multiply, 4 fft y inverse, 5 fftx inverse + epilogue.
+struct KTimer {
+    int stage = -1;
+    int f32 = 1;
+    cudaEvent_t* ev = nullptr;   // 2 * cap events
+    int cap = 0;
+    int used = 0;
+    int open = 0;
+    double ms = 0.0;             // flushed total
+    long long launches = 0;      // flushed launches
+};
+void ktimer_mark(KTimer* t, int stage, bool f32, cudaStream_t st, int end);
+void ktimer_flush(KTimer* t);
 
 struct Medium {
     Dims d;
     const void* dC;      // [21][N] of T
     const void* drho;    // [N] of T
+    KTimer* timer;       // optional stage timer
 };
 
 struct Plans {

@@ -65,6 +65,8 @@ struct Store {
     ApplySys<float>* a32 = nullptr;
     int* flag = nullptr;
     int* h_pinned = nullptr;   // pinned host ints for readbacks
+    unsigned long long* counts = nullptr;  // device: executed system applies [FP64, FP32]
+    KTimer timer;
     SolverWS ws;
 };
 
@@ -136,7 +138,11 @@ void store_release(Store* s) {
     cudaFree(s->dC64); cudaFree(s->drho64); cudaFree(s->dC32); cudaFree(s->drho32);
     cudaFree(s->tw64); cudaFree(s->tw32);
     cudaFree(s->w1_64); cudaFree(s->w2_64); cudaFree(s->w1_32); cudaFree(s->w2_32);
-    cudaFree(s->a64); cudaFree(s->a32); cudaFree(s->flag);
+    cudaFree(s->a64); cudaFree(s->a32); cudaFree(s->flag); cudaFree(s->counts);
+    if (s->timer.ev) {
+        for (int i = 0; i < 2 * s->timer.cap; ++i) cudaEventDestroy(s->timer.ev[i]);
+        delete[] s->timer.ev;
+    }
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
     cudaFree(s->ws.block);
     delete s;
@@ -162,6 +168,7 @@ Medium medium_of(Store* s, int prec32) {
     m.d = s->d;
     m.dC = prec32 ? (const void*)s->dC32 : (const void*)s->dC64;
     m.drho = prec32 ? (const void*)s->drho32 : (const void*)s->drho64;
+    m.timer = &s->timer;
     return m;
 }
 
@@ -271,6 +278,8 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     CKB(cudaMalloc(&s->a64, sizeof(ApplySys<double>)));
     CKB(cudaMalloc(&s->a32, sizeof(ApplySys<float>)));
     CKB(cudaMalloc(&s->flag, sizeof(int)));
+    CKB(cudaMalloc(&s->counts, 2 * sizeof(unsigned long long)));
+    CKB(cudaMemsetAsync(s->counts, 0, 2 * sizeof(unsigned long long), s->st));
     CKB(cudaMallocHost(&s->h_pinned, 16 * sizeof(int)));
     rc = build_spectrum(h);
     if (rc != LSM_OK) return bail(rc);
@@ -348,6 +357,7 @@ static lsm_status apply_one(lsm_t h, const void* u, void* Au, bool adjoint) {
     a.w2 = f32 ? (C*)s->w2_32 : (C*)s->w2_64;
     a.omega2 = (T)(h->omega * h->omega);
     a.run = nullptr;
+    a.count = s->counts + (f32 ? 1 : 0);
     ApplySys<T>* dev = f32 ? (ApplySys<T>*)s->a32 : (ApplySys<T>*)s->a64;
     CK(h, cudaMemcpyAsync(dev, &a, sizeof(a), cudaMemcpyHostToDevice, s->st));
     const Plans& pl = f32 ? s->pl32 : s->pl64;
@@ -508,6 +518,7 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, double
         CK(h0, bcg_xr<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
         CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(h0, cudaStreamSynchronize(st));
+        ktimer_flush(&s->timer);
         n_active = s->h_pinned[0];
     }
     out.resize(nsys);
@@ -558,6 +569,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
             V[i].x = (double2*)x[i];
             V[i].r = k[0]; V[i].rh = k[1]; V[i].p = k[2]; V[i].v = k[3]; V[i].s = k[4]; V[i].t = k[5];
             ApplySys<double> a;
+            a.count = s->counts;
             a.ghat = hs[i]->ghat64;
             a.w1 = (double2*)w.w1[i];
             a.w2 = (double2*)w.w2[i];
@@ -611,6 +623,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
             V[i].r = k[1]; V[i].rh = k[2]; V[i].p = k[3]; V[i].v = k[4]; V[i].s = k[5]; V[i].t = k[6];
             V[i].b = k[7];   // normalised FP32 residual
             ApplySys<float> a;
+            a.count = s->counts + 1;
             a.ghat = hs[i]->ghat32;
             a.w1 = (float2*)w.w1[i];
             a.w2 = (float2*)w.w2[i];
@@ -618,6 +631,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
             a.u = V[i].p; a.out = V[i].v; a.run = &w.st[i].run_v; sv[i] = a;
             a.u = V[i].s; a.out = V[i].t; a.run = &w.st[i].run_t; stt[i] = a;
             ApplySys<double> d;
+            d.count = s->counts;
             d.ghat = hs[i]->ghat64;
             d.w1 = w.w1d[i];
             d.w2 = w.w2d[i];
@@ -654,6 +668,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
                                 pt, n3, nsys, w.n_active, st, &h0->nl));
             CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(h0, cudaStreamSynchronize(st));
+            ktimer_flush(&s->timer);
             if (s->h_pinned[0] == 0 || outer >= h0->o.max_outer) break;
             CK(h0, mix_down((double2* const*)(P + 2 * nsys), (float2* const*)(P + 3 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
             for (int i = 0; i < nsys; ++i) CK(h0, cudaMemsetAsync(w.kry[i * KRY + 0], 0, n3 * sizeof(float2), st));
@@ -688,4 +703,41 @@ extern "C" lsm_status lsm_solve(lsm_t h, const void* b, void* x, int* iters, dou
     const void* bb[1] = {b};
     void* xx[1] = {x};
     return lsm_solve_batched(1, &h, bb, xx, iters, relres, nullptr);
+}
+
+extern "C" lsm_status lsm_timer_start(lsm_t h, int stage, int precision) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_timer_start: null handle");
+    if (stage < -1 || stage > 5 || (precision != LSM_FP64 && precision != LSM_MIXED))
+        return fail(h, LSM_ERR_ARG, "lsm_timer_start: stage must be -1..5, precision LSM_FP64 or LSM_MIXED");
+    Store* s = h->s;
+    CK(h, cudaStreamSynchronize(s->st));
+    KTimer& t = s->timer;
+    if (!t.ev) {
+        t.cap = 4096;
+        t.ev = new cudaEvent_t[2 * t.cap];
+        for (int i = 0; i < 2 * t.cap; ++i) CK(h, cudaEventCreate(&t.ev[i]));
+    }
+    t.stage = stage;
+    t.f32 = precision == LSM_MIXED ? 1 : 0;
+    t.used = 0;
+    t.open = 0;
+    t.ms = 0.0;
+    t.launches = 0;
+    CK(h, cudaMemsetAsync(s->counts, 0, 2 * sizeof(unsigned long long), s->st));
+    CK(h, cudaStreamSynchronize(s->st));
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_timer_read(lsm_t h, double* ms, long long* launches, long long* applies64, long long* applies32) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_timer_read: null handle");
+    Store* s = h->s;
+    CK(h, cudaStreamSynchronize(s->st));
+    ktimer_flush(&s->timer);
+    unsigned long long c[2] = {0, 0};
+    CK(h, cudaMemcpy(c, s->counts, sizeof(c), cudaMemcpyDeviceToHost));
+    if (ms) *ms = s->timer.ms;
+    if (launches) *launches = s->timer.launches;
+    if (applies64) *applies64 = (long long)c[0];
+    if (applies32) *applies32 = (long long)c[1];
+    return LSM_OK;
 }

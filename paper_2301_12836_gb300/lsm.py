@@ -33,7 +33,8 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_apply", "lsm_apply_c64",
-           "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_launch_count", "lsm_destroy", "lsm_last_error")
+           "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
+           "lsm_destroy", "lsm_last_error")
 
 
 class lsm_opts(ct.Structure):
@@ -77,6 +78,11 @@ def load(path: str = LIB_PATH):
     lib.lsm_solve_batched.restype = i
     lib.lsm_launch_count.argtypes = [vp]
     lib.lsm_launch_count.restype = ct.c_longlong
+    lib.lsm_timer_start.argtypes = [vp, i, i]
+    lib.lsm_timer_start.restype = i
+    lib.lsm_timer_read.argtypes = [vp, ct.POINTER(d), ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong),
+                                   ct.POINTER(ct.c_longlong)]
+    lib.lsm_timer_read.restype = i
     lib.lsm_destroy.argtypes = [vp]
     lib.lsm_destroy.restype = None
     lib.lsm_last_error.argtypes = [vp]
@@ -201,3 +207,15 @@ def lsm_solve_batched(hs, bs, xs, check=True):
 
 def lsm_launch_count(h: Handle) -> int:
     return int(load().lsm_launch_count(h.ptr))
+
+
+def lsm_timer_start(h: Handle, stage: int, precision: int) -> None:
+    _check(load().lsm_timer_start(h.ptr, int(stage), int(precision)), h.ptr)
+
+
+def lsm_timer_read(h: Handle):
+    """Returns (milliseconds, launches, FP64 system applies, FP32 system applies) since lsm_timer_start."""
+    ms = ct.c_double(0.0)
+    nl, a64, a32 = ct.c_longlong(0), ct.c_longlong(0), ct.c_longlong(0)
+    _check(load().lsm_timer_read(h.ptr, ct.byref(ms), ct.byref(nl), ct.byref(a64), ct.byref(a32)), h.ptr)
+    return ms.value, nl.value, a64.value, a32.value
