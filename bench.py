@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--systems", type=int, default=8, help="moment tensors solved together per step")
     ap.add_argument("--timer-stage", type=int, default=3)
+    ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
@@ -266,6 +267,8 @@ def main():
     dC = torch.from_numpy(med.dC).cuda().contiguous()
     drho = torch.from_numpy(med.drho).cuda().contiguous()
     opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000)
+    if args.inner_tol:
+        opts.inner_tol = args.inner_tol
     handles = {}
     t_setup = time.perf_counter()
     base = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[0]], opts)

@@ -67,7 +67,9 @@ typedef struct {
                           LSM_GREEN_PAPER: near field Eq. A.4 + far field Eq. A.5. */
     double tol;        /* target relative residual of Eq. 22 (default 1e-10) */
     int maxit;         /* BiCGSTAB iteration limit per solve (FP64) or per inner solve (mixed) */
-    double inner_tol;  /* mixed: relative tolerance of each FP32 inner solve (default 1e-4) */
+    double inner_tol;  /* mixed: the tightest relative tolerance an FP32 inner solve is asked for.
+                          Each inner solve aims at 0.1 * tol / (current FP64 relres),
+                          clamped to [inner_tol, 0.1] (default 1e-6) */
     int max_outer;     /* mixed: refinement steps limit (default 8) */
 } lsm_opts;
 

@@ -180,7 +180,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->green = LSM_GREEN_EXACT;
     o->tol = 1e-10;
     o->maxit = 1000;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 1e-6;
     o->max_outer = 8;
 }
 
@@ -470,8 +470,8 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
 
 // Run BiCGSTAB on nsys systems whose vectors/apply arguments are already on the device.
 template <typename T>
-lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, double tol, int maxit, bool x_zero,
-                        const MixState* skip, std::vector<BcgState>& out) {
+lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const std::vector<double>& tol, int maxit,
+                        bool x_zero, const MixState* skip, std::vector<BcgState>& out) {
     Store* s = h0->s;
     SolverWS& w = s->ws;
     const long long n3 = w.n3;
@@ -491,7 +491,7 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, double
     for (int i = 0; i < nsys; ++i) {
         BcgState& b = init[i];
         memset(&b, 0, sizeof(b));
-        b.tol2 = tol * tol;
+        b.tol2 = tol[i] * tol[i];
         b.maxit = maxit;
         b.active = 0;
     }
@@ -585,7 +585,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
         CK(h0, cudaMemcpyAsync(w.sys_x, sx.data(), nsys * sizeof(sx[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys64, a64.data(), nsys * sizeof(a64[0]), cudaMemcpyHostToDevice, st));
         std::vector<BcgState> fin;
-        rc = run_bicgstab<double>(h0, hs, nsys, tol, h0->o.maxit, false, nullptr, fin);
+        rc = run_bicgstab<double>(h0, hs, nsys, std::vector<double>(nsys, tol), h0->o.maxit, false, nullptr, fin);
         if (rc != LSM_OK) return rc;
         for (int i = 0; i < nsys; ++i) {
             it_out[i] = fin[i].iters;
@@ -658,22 +658,33 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
         CK(h0, cudaMemcpyAsync(P, hp.data(), 6 * nsys * sizeof(void*), cudaMemcpyHostToDevice, st));
         for (int i = 0; i < nsys; ++i) ms[i].run = 1;
         CK(h0, cudaMemcpyAsync(w.ms, ms.data(), nsys * sizeof(MixState), cudaMemcpyHostToDevice, st));
+        // a zero initial guess needs no FP64 apply: its residual is b
+        CK(h0, mix_xnorm((const double2* const*)(P + 4 * nsys), w.ms, pt, n3, nsys, st, &h0->nl));
         Medium m64 = medium_of(s, 0);
         const int nblk = pt.nblk;
+        std::vector<double> itol(nsys, h0->o.inner_tol);
         for (int outer = 0;; ++outer) {
             cudaError_t e = launch_apply<double>(m64, s->pl64, w.sys64, nsys, st, &h0->nl);
             if (e != cudaSuccess) return cuda_fail(h0, e, "FP64 residual apply");
             CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
             CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms,
                                 pt, n3, nsys, w.n_active, st, &h0->nl));
-            CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
             CK(h0, cudaStreamSynchronize(st));
             ktimer_flush(&s->timer);
-            if (s->h_pinned[0] == 0 || outer >= h0->o.max_outer) break;
+            int n_act = 0;
+            for (int i = 0; i < nsys; ++i) n_act += !ms[i].done;
+            if (n_act == 0 || outer >= h0->o.max_outer) break;
+            // each inner FP32 solve aims a decade below what the outer target still needs,
+            // never tighter than inner_tol (the floor FP32 arithmetic can certify)
+            for (int i = 0; i < nsys; ++i) {
+                const double need = ms[i].relres > 0 ? 0.1 * tol / ms[i].relres : 1.0;
+                itol[i] = need < h0->o.inner_tol ? h0->o.inner_tol : (need > 0.1 ? 0.1 : need);
+            }
             CK(h0, mix_down((double2* const*)(P + 2 * nsys), (float2* const*)(P + 3 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
             for (int i = 0; i < nsys; ++i) CK(h0, cudaMemsetAsync(w.kry[i * KRY + 0], 0, n3 * sizeof(float2), st));
             std::vector<BcgState> fin;
-            rc = run_bicgstab<float>(h0, hs, nsys, h0->o.inner_tol, h0->o.maxit, true, w.ms, fin);
+            rc = run_bicgstab<float>(h0, hs, nsys, itol, h0->o.maxit, true, w.ms, fin);
             if (rc != LSM_OK) return rc;
             for (int i = 0; i < nsys; ++i) it_out[i] += fin[i].iters;
             CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));

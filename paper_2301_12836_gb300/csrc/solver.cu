@@ -291,9 +291,10 @@ __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restric
     const double2* B = b[sys];
     const double2* AX = ax[sys];
     double2* R = r64[sys];
+    const int xz = ms[sys].xzero;
     double v[2] = {0.0, 0.0};
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const double2 bb = B[i], a = AX[i];
+        const double2 bb = B[i], a = xz ? make_double2(0.0, 0.0) : AX[i];
         const double2 r = make_double2(bb.x - a.x, bb.y - a.y);
         R[i] = r;
         v[0] += bb.x * bb.x + bb.y * bb.y;
@@ -311,6 +312,22 @@ __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restric
     }
 }
 
+__global__ void __launch_bounds__(VTH) k_mix_xnorm(const double2* const* __restrict__ x64, MixState* __restrict__ ms,
+                                                   Partials pt, long long n) {
+    const int sys = blockIdx.y;
+    const double2* X = x64[sys];
+    double v[1] = {0.0};
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const double2 x = X[i];
+        v[0] += x.x * x.x + x.y * x.y;
+    }
+    double tot[1];
+    if (grid_sum<1>(v, pt, sys, &ms[sys].counter, tot)) {
+        ms[sys].xzero = tot[0] == 0.0 ? 1 : 0;
+        ms[sys].run = !ms[sys].xzero;
+    }
+}
+
 __global__ void __launch_bounds__(VTH) k_mix_down(double2* const* __restrict__ r64, float2* const* __restrict__ r32,
                                                   const MixState* __restrict__ ms, long long n) {
     const int sys = blockIdx.y;
@@ -325,12 +342,13 @@ __global__ void __launch_bounds__(VTH) k_mix_down(double2* const* __restrict__ r
 }
 
 __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64, float2* const* __restrict__ d32,
-                                                const MixState* __restrict__ ms, long long n) {
+                                                MixState* __restrict__ ms, long long n) {
     const int sys = blockIdx.y;
     if (ms[sys].done) return;
     const double sc = sqrt(ms[sys].rnorm2);
     double2* X = x64[sys];
     const float2* D = d32[sys];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ms[sys].xzero = 0;
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const float2 d = D[i];
         double2 x = X[i];
@@ -408,7 +426,13 @@ cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms
     if (nl) *nl += 1;
     return cudaGetLastError();
 }
-cudaError_t mix_up(double2* const* x64, float2* const* d32, const MixState* ms, long long n, int nsys, int nblk, cudaStream_t s,
+cudaError_t mix_xnorm(const double2* const* x64, MixState* ms, Partials pt, long long n, int nsys, cudaStream_t s,
+                      long long* nl) {
+    k_mix_xnorm<<<dim3(pt.nblk, nsys), VTH, 0, s>>>(x64, ms, pt, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, long long n, int nsys, int nblk, cudaStream_t s,
                    long long* nl) {
     k_mix_up<<<dim3(nblk, nsys), VTH, 0, s>>>(x64, d32, ms, n);
     if (nl) *nl += 1;

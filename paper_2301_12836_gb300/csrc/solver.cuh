@@ -42,6 +42,7 @@ struct MixState {
     double tol;
     int done;
     int run;            // FP64 residual apply runs
+    int xzero;          // the iterate is exactly zero: the residual is b, no apply needed
     unsigned int counter;
 };
 
@@ -68,11 +69,14 @@ cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long 
                    cudaStream_t s, long long* nl);
 
 // mixed refinement: r64 = b - ax (relres), r32 = r64/||r64||, x64 += ||r64|| d32
+// xzero = (||x||^2 == 0) per system; the FP64 residual apply is skipped for those systems
+cudaError_t mix_xnorm(const double2* const* x64, MixState* ms, Partials pt, long long n, int nsys, cudaStream_t s,
+                      long long* nl);
 cudaError_t mix_residual(const double2* const* b, const double2* const* ax, double2* const* r64, MixState* ms,
                          Partials pt, long long n, int nsys, int* n_active, cudaStream_t s, long long* nl);
 cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms, long long n, int nsys, int nblk,
                      cudaStream_t s, long long* nl);
-cudaError_t mix_up(double2* const* x64, float2* const* d32, const MixState* ms, long long n, int nsys, int nblk,
+cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, long long n, int nsys, int nblk,
                    cudaStream_t s, long long* nl);
 
 int vec_blocks(long long n);

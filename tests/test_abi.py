@@ -47,7 +47,7 @@ def test_default_opts(lib):
     from paper_2301_12836_gb300 import lsm
     o = lsm.lsm_default_opts()
     assert o.precision == lsm.LSM_FP64 and o.green == lsm.LSM_GREEN_EXACT
-    assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-4 and o.max_outer >= 2
+    assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-6 and o.max_outer >= 2
 
 
 @pytest.mark.parametrize("n,ok", [((2, 2, 2), True), ((1, 4, 4), False), ((7, 4, 4), False),
