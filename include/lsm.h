@@ -190,6 +190,24 @@ long long lsm_launch_count(lsm_t h);
 lsm_status lsm_timer_start(lsm_t h, int stage, int precision);
 lsm_status lsm_timer_read(lsm_t h, double *ms, long long *launches, long long *applies64, long long *applies32);
 
+/*
+ * FP64 operator apply that allocates nothing (the paper has no counterpart; this is a service
+ * to callers that cannot call cudaMalloc when they apply the operator: code running while its
+ * stream is captured into a CUDA graph, serving loops whose device memory is reserved up front
+ * by another allocator, latency-critical loops that must not meet an out-of-memory error).
+ * Same result as lsm_apply; the handle itself must already exist (lsm_create allocates).
+ *   u, Au  device complex128, 3 * nz*ny*nx; u != Au.
+ * The workspace is one library-wide array in device global memory of 64 MiB, present on every
+ * GPU that loads the library until the process exits.  A grid needs about
+ * 384 * nx * ny * (nz + 1) bytes of it (cubic grids up to 54^3 fit); a grid that needs more is
+ * rejected with LSM_ERR_ARG.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
+ * the one array and each call leaves its contents behind; nothing in it needs to start at zero.
+ * Calls whose work overlaps on the GPU (different streams, or different handles without
+ * ordering between them) race on the array: order them on one stream.
+ */
+lsm_status lsm_apply_static(lsm_t h, const void *u, void *Au);
+
 /* Release every device buffer the handle owns (shared contrast when its last user goes). */
 void lsm_destroy(lsm_t h);
 

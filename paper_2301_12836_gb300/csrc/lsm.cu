@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -750,5 +751,97 @@ extern "C" lsm_status lsm_timer_read(lsm_t h, double* ms, long long* launches, l
     if (launches) *launches = s->timer.launches;
     if (applies64) *applies64 = (long long)c[0];
     if (applies32) *applies32 = (long long)c[1];
+    return LSM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Operator apply without any device allocation.
+//
+// lsm_apply allocates its FP64 workspace with cudaMalloc on a handle's first apply.  Some callers
+// cannot allocate at that point: code running while a stream is being captured into a CUDA graph
+// (device allocation is not a capturable operation), serving loops that have reserved all device
+// memory up front through another allocator and forbid further cudaMalloc calls, or callers that
+// must not risk an out-of-memory failure in the middle of a time-critical loop.
+// lsm_apply_static gives them the same FP64 apply with its workspace taken from one library-wide
+// array in device global memory (g_static_scratch, STATIC_SCRATCH_BYTES per device that loads the
+// library, held until the process exits).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t STATIC_SCRATCH_BYTES = 64ull << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+void* g_static_addr[MAX_DEVICES] = {nullptr};
+std::mutex g_static_mu;
+
+// Device address of g_static_scratch on the current device; looked up once per device (the
+// host-side symbol is only a stand-in and must never be handed to a kernel).
+cudaError_t static_scratch_addr(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// bytes of the static array one apply on an n[0] x n[1] x n[2] grid uses
+static size_t static_apply_bytes(const int n[3]) {
+    Dims d;
+    d.nx = n[0]; d.ny = n[1]; d.nz = n[2];
+    d.Lx = 2 * d.nx; d.Ly = 2 * d.ny; d.Lz = 2 * d.nz;
+    d.ex = d.nx + 2; d.ey = d.ny + 2; d.ez = d.nz + 2;
+    d.N = (long long)d.nx * d.ny * d.nz;
+    long long e1, e2;
+    apply_ws_elems(d, &e1, &e2);
+    return align_up(sizeof(ApplySys<double>)) + align_up(e1 * sizeof(double2)) + align_up(e2 * sizeof(double2));
+}
+
+extern "C" lsm_status lsm_apply_static(lsm_t h, const void* u, void* Au) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_apply_static: null handle");
+    if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply_static: u and Au must be distinct non-null device buffers");
+    Store* s = h->s;
+    const int n[3] = {s->d.nx, s->d.ny, s->d.nz};
+    const size_t need = static_apply_bytes(n);
+    if (need > STATIC_SCRATCH_BYTES) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "lsm_apply_static: grid %dx%dx%d needs %zu bytes of scratch, more than the %zu-byte static array",
+                 n[0], n[1], n[2], need, (size_t)STATIC_SCRATCH_BYTES);
+        return fail(h, LSM_ERR_ARG, msg);
+    }
+    void* base = nullptr;
+    CK(h, static_scratch_addr(&base));
+    long long e1, e2;
+    apply_ws_elems(s->d, &e1, &e2);
+    char* p = (char*)base;
+    ApplySys<double>* dev_args = (ApplySys<double>*)p;
+    double2* w1 = (double2*)(p + align_up(sizeof(ApplySys<double>)));
+    double2* w2 = (double2*)((char*)w1 + align_up(e1 * sizeof(double2)));
+    // every workspace element the apply reads is written earlier in the same apply, so nothing
+    // in the array has to start at zero
+    ApplySys<double> a;
+    a.u = (const double2*)u;
+    a.out = (double2*)Au;
+    a.ghat = h->ghat64;
+    a.w1 = w1;
+    a.w2 = w2;
+    a.omega2 = h->omega * h->omega;
+    a.run = nullptr;
+    a.count = nullptr;
+    CK(h, cudaMemcpyAsync(dev_args, &a, sizeof(a), cudaMemcpyHostToDevice, s->st));
+    Medium m = medium_of(s, 0);
+    m.timer = nullptr;
+    cudaError_t e = launch_apply<double>(m, s->pl64, dev_args, 1, s->st, &h->nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lsm_apply_static");
     return LSM_OK;
 }

@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_apply", "lsm_apply_c64",
            "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
-           "lsm_destroy", "lsm_last_error")
+           "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
 
 class lsm_opts(ct.Structure):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH):
     lib.lsm_timer_read.argtypes = [vp, ct.POINTER(d), ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong),
                                    ct.POINTER(ct.c_longlong)]
     lib.lsm_timer_read.restype = i
+    lib.lsm_apply_static.argtypes = [vp, vp, vp]
+    lib.lsm_apply_static.restype = i
     lib.lsm_destroy.argtypes = [vp]
     lib.lsm_destroy.restype = None
     lib.lsm_last_error.argtypes = [vp]
@@ -219,3 +221,9 @@ def lsm_timer_read(h: Handle):
     nl, a64, a32 = ct.c_longlong(0), ct.c_longlong(0), ct.c_longlong(0)
     _check(load().lsm_timer_read(h.ptr, ct.byref(ms), ct.byref(nl), ct.byref(a64), ct.byref(a32)), h.ptr)
     return ms.value, nl.value, a64.value, a32.value
+
+
+def lsm_apply_static(h: Handle, u: torch.Tensor, Au: torch.Tensor) -> None:
+    """FP64 apply whose workspace is the library's static device array (no device allocation)."""
+    _check(load().lsm_apply_static(h.ptr, _ptr(u, torch.complex128, 3 * h.N), _ptr(Au, torch.complex128, 3 * h.N)),
+           h.ptr)
