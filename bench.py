@@ -32,7 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "LS matvecs/s and solves/s at 128³ (FP32+refine vs FP64), % of HBM roofline"
-STAGES = {0: "k_stress", 1: "k_div_fftx", 2: "k_strided(y fwd)", 3: "k_fftz_green", 4: "k_strided(y inv)", 5: "k_fftx_out"}
+STAGES = {0: "k_stress", 1: "k_divq+x fft", 2: "y fft", 3: "z fft+green", 4: "y ifft", 5: "x ifft+epilogue"}
 
 
 def parse():
@@ -45,7 +45,6 @@ def parse():
     ap.add_argument("--grid", type=int, default=None, help="override the grid size (small profiling cases)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--systems", type=int, default=8, help="moment tensors solved together per step")
-    ap.add_argument("--timer-stage", type=int, default=3)
     ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -62,15 +61,39 @@ def stage_bytes(stage, n, b, c):
     Lx, Ly = 2 * nx, 2 * ny
     ex, ey, ez = nx + 2, ny + 2, nz + 2
     NO = (nx + 1) * (ny + 1) * (nz + 1)
-    del ex
+    E = ex * ey * ez
     return {
         0: (3 * b + 21 * c + 6 * b) * N,
-        1: 9 * N * b + N * c + 3 * ez * ey * Lx * b,
+        1: 9 * N * b + N * c + 6 * E * b + 3 * ez * ey * Lx * b,
         2: 3 * ez * ey * Lx * b + 3 * ez * Ly * Lx * b,
         3: 3 * ez * Ly * Lx * b + 6 * NO * b + 3 * nz * Ly * Lx * b,
         4: 3 * nz * Ly * Lx * b + 3 * nz * ny * Lx * b,
         5: 3 * nz * ny * Lx * b + 3 * N * b + 3 * N * b,
     }[stage]
+
+
+def stage_flops(stage, n):
+    """Model flops per system apply: 5 L log2 L per complex FFT line, 6 per complex multiply,
+    2 per complex add, 4 per real-by-complex multiply-add."""
+    import math
+    nx, ny, nz = n
+    N = nx * ny * nz
+    Lx, Ly, Lz = 2 * nx, 2 * ny, 2 * nz
+    ex, ey, ez = nx + 2, ny + 2, nz + 2
+    fft = lambda L: 5.0 * L * math.log2(L)  # noqa: E731
+    return {
+        0: N * (9 * 2 + 36 * 4),
+        1: ex * ey * ez * 3 * (6 * 2 + 2 + 4) + 3 * ey * ez * fft(Lx),
+        2: 3 * ez * Lx * fft(Ly),
+        3: 2 * 3 * Lx * Ly * fft(Lz) + Lx * Ly * Lz * (9 * 6 + 6 * 2),
+        4: 3 * nz * Lx * fft(Ly),
+        5: 3 * ny * nz * fft(Lx) + 3 * N * 2,
+    }[stage]
+
+
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock per SM (1/64 of the
+# 128 FP32 lanes) x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def peaks():
@@ -302,7 +325,7 @@ def main():
         step(s)
     stats = {"iters": [], "relres": []}
     launches0 = sum(lsm.lsm_launch_count(h) for h in handles.values())
-    lsm.lsm_timer_start(base, args.timer_stage, prec)
+    lsm.lsm_timer_start(base, True)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
@@ -325,7 +348,7 @@ def main():
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    t_ms, t_launch, a64, a32 = lsm.lsm_timer_read(base)
+    st_ms, st_launch, (a64, a32) = lsm.lsm_timer_read(base)
     launches = sum(lsm.lsm_launch_count(h) for h in handles.values()) - launches0
     solves = args.steps * nsys
     applies = a64 + a32
@@ -339,18 +362,39 @@ def main():
     else:
         ms_max, applies_all, solves_all, launches_all = ms, float(applies), float(solves), float(launches)
     value = applies_all / (ms_max / 1e3)
-    # roofline of the timed stage (FP32 applies in the mixed form, FP64 in the plain one)
-    bsz, csz = (8, 4) if prec == lsm.LSM_MIXED else (16, 8)
-    napp = a32 if prec == lsm.LSM_MIXED else a64
-    per_app = stage_bytes(args.timer_stage, med.n, bsz, csz)
+    # per-stage rooflines: FP32 stages against HBM (algorithmic bytes), FP64 stages against the
+    # FP64 pipe (model flops); the dominant stage (largest share of the timed region) is reported
     peak, peak_kind = peaks()
-    achieved = per_app * napp / (t_ms / 1e3) / 1e9 if t_ms > 0 else 0.0
-    traffic = traffic_from_profile(args.timer_stage, args.precision, med.n)
-    roof = {"bound": "hbm", "kernel": STAGES[args.timer_stage] + ("<float>" if prec == lsm.LSM_MIXED else "<double>"),
-            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_system_apply": per_app,
-            "timed_launches": t_launch, "timed_ms": round(t_ms, 3),
-            "share_of_step": round(t_ms / ms, 4) if ms > 0 else None}
+    stages = []
+    for slot in range(12):
+        if st_launch[slot] == 0 or st_ms[slot] <= 0:
+            continue
+        f32 = slot >= 6
+        stage = slot % 6
+        napp = a32 if f32 else a64
+        name = STAGES[stage] + ("<float>" if f32 else "<double>")
+        rec = {"kernel": name, "ms": round(st_ms[slot], 3), "launches": st_launch[slot],
+               "share_of_step": round(st_ms[slot] / ms, 4)}
+        if f32:
+            b = stage_bytes(stage, med.n, 8, 4)
+            ach = b * napp / (st_ms[slot] / 1e3) / 1e9
+            rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": b})
+        else:
+            fl = stage_flops(stage, med.n)
+            ach = fl * napp / (st_ms[slot] / 1e3) / 1e12
+            rec.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                        "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                        "model_flops_per_system_apply": fl})
+        stages.append(rec)
+    stages.sort(key=lambda r: -r["ms"])
+    dom = dict(stages[0]) if stages else {}
+    if dom:
+        prec_s = "mixed" if dom["kernel"].endswith("<float>") else "fp64"
+        stage_id = [k for k, v in STAGES.items() if dom["kernel"].startswith(v)][0]
+        dom["traffic"] = traffic_from_profile(stage_id, prec_s, med.n)
+        dom["peak_kind"] = peak_kind if dom["bound"] == "hbm" else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"
+    roof = dom
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "matvec/s", "n_gpus": world, "steps": args.steps,
@@ -362,7 +406,7 @@ def main():
         "iterations_mean": round(float(np.mean(stats["iters"])), 2),
         "relres_max": float(np.max(stats["relres"])),
         "setup_s": round(t_setup, 2),
-        "roofline": roof, "gpu_launches": int(launches_all),
+        "roofline": roof, "stages": stages, "gpu_launches": int(launches_all),
     }
     cs = sampler.summary()
     if cs:
@@ -371,14 +415,14 @@ def main():
     # end to end through the C ABI with host buffers: results copied to pinned host memory each step
     if not args.no_e2e:
         host = [torch.empty(N3, dtype=torch.complex128, pin_memory=True) for _ in range(nsys)]
-        lsm.lsm_timer_start(base, -1, prec)
+        lsm.lsm_timer_start(base, False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(args.warmup, steps_total):
             step(s, host_out=host)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        _, _, e64, e32 = lsm.lsm_timer_read(base)
+        _, _, (e64, e32) = lsm.lsm_timer_read(base)
         line["e2e"] = {"value": round((e64 + e32) / te, 3), "unit": "matvec/s",
                        "h2d_bytes_per_step": nsys * 9 * 8, "d2h_bytes_per_step": nsys * N3 * 16,
                        "solves_per_s": round(solves / te, 4)}
@@ -393,13 +437,13 @@ def main():
         for j in range(nsys):
             lsm.lsm_source(h64, M[j], xs[j], b[j])
             x[j].zero_()
-        lsm.lsm_timer_start(h64, -1, lsm.LSM_FP64)
+        lsm.lsm_timer_start(h64, False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         code, its, rrs, sts = lsm.lsm_solve_batched([h64] * nsys, b, x, check=False)
         torch.cuda.synchronize()
         tf = time.perf_counter() - t0
-        _, _, f64, _ = lsm.lsm_timer_read(h64)
+        _, _, (f64, _) = lsm.lsm_timer_read(h64)
         line["fp64_form"] = {"solves_per_s": round(nsys / tf, 4), "matvecs_per_s": round(f64 / tf, 3),
                              "iterations_mean": float(np.mean(its)), "relres_max": float(np.max(rrs)),
                              "status": lsm.STATUS_NAMES.get(code), "frequency_hz": freqs[fidx[-1]]}

@@ -175,20 +175,19 @@ long long lsm_launch_count(lsm_t h);
 
 /*
  * Diagnostics for roofline measurement (no counterpart in the paper).
- * lsm_timer_start: from now on, record a CUDA event pair around every launch of
- * one stage of the operator apply, on the handle's stream, for applies in the
- * given precision (LSM_FP64, or LSM_MIXED for the FP32 applies), on every
- * handle that shares h's medium; also zero the executed-apply counters.
- * Stages: 0 strain + contraction, 1 contrast source + x FFT, 2 y FFT,
- * 3 z FFT + Green multiply + inverse z FFT, 4 inverse y FFT,
- * 5 inverse x FFT + epilogue; -1 times nothing.  Synchronises the stream.
- * lsm_timer_read: synchronise, then report the total milliseconds and launches
- * of the timed stage, and the number of system-level operator applies executed
- * in FP64 and FP32 since lsm_timer_start (systems masked out of a batched
- * launch are not counted).  Any out-pointer may be NULL.
+ * lsm_timer_start(h, enable): zero the totals and the executed-apply counters, and (enable != 0)
+ * from now on record a CUDA event pair on the handle's stream around every launch of every stage
+ * of the operator apply, on every handle that shares h's medium.  Stages: 0 strain +
+ * contraction, 1 contrast source + x FFT, 2 y FFT, 3 z FFT + Green multiply + inverse z FFT,
+ * 4 inverse y FFT, 5 inverse x FFT + epilogue.  Synchronises the stream.
+ * lsm_timer_read: synchronise, then write total milliseconds and launches per slot
+ * (slot = 6 * p + stage, p = 0 for FP64 applies, 1 for FP32 applies) and the number of
+ * system-level operator applies executed in FP64 (applies[0]) and FP32 (applies[1]) since
+ * lsm_timer_start; systems masked out of a batched launch are not counted.  Any out-pointer
+ * may be NULL.
  */
-lsm_status lsm_timer_start(lsm_t h, int stage, int precision);
-lsm_status lsm_timer_read(lsm_t h, double *ms, long long *launches, long long *applies64, long long *applies32);
+lsm_status lsm_timer_start(lsm_t h, int enable);
+lsm_status lsm_timer_read(lsm_t h, double ms[12], long long launches[12], long long applies[2]);
 
 /*
  * FP64 operator apply that allocates nothing (the paper has no counterpart; this is a service

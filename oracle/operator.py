@@ -340,3 +340,30 @@ def dense_matrix(medium, omega, mode="exact"):
     T = _green.kernel_table(n, h, omega, medium.lam0, medium.mu0, medium.rho0, mode)
     K = kernel_matrix(n, T)
     return np.eye(3 * N, dtype=np.complex128) - K @ W
+
+
+def apply_at_points(u, medium, omega, points, mode="exact"):
+    """(A u)(x) at a few nodes x by direct summation over the extended grid; any grid size.
+
+    points: iterable of node indices (ix, iy, iz).  Returns an array (len(points), 3) complex.
+    The contrast source q is formed on the whole extended grid [-1, n]^3 (as in
+    ``contrast_source``); each output then sums T(x - x') q(x') over x' with the kernel of
+    ``green.kernel_table`` evaluated at exactly the offsets needed.
+    """
+    nx, ny, nz = medium.n
+    h = medium.h
+    q = contrast_source(u, medium.dC, medium.drho, h, omega)
+    ext = [np.arange(-1, m + 1) for m in (nx, ny, nz)]
+    out = []
+    for ix, iy, iz in points:
+        MZ, MY, MX = np.meshgrid(iz - ext[2], iy - ext[1], ix - ext[0], indexing="ij")
+        nyq = (np.abs(MX) >= nx) | (np.abs(MY) >= ny) | (np.abs(MZ) >= nz)
+        self_ = (MX == 0) & (MY == 0) & (MZ == 0)
+        off = np.stack([MX, MY, MZ], axis=-1).astype(np.float64) * h
+        off[nyq | self_] = h  # placeholder, overwritten below
+        T = _green.green(off, omega, medium.lam0, medium.mu0, medium.rho0, mode) * h ** 3
+        T[nyq] = 0.0
+        T[self_] = _green.self_cell(h, omega, medium.lam0, medium.mu0, medium.rho0)
+        us = np.einsum("zyxij,jzyx->i", T, q)
+        out.append(u[:, iz, iy, ix] - us)
+    return np.array(out)

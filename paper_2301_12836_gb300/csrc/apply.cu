@@ -2,23 +2,62 @@
 //
 // One application A u = u - crop( G * q ), q_j = sum_k D_k sigma_jk + w^2 drho u_j, runs as:
 //   k_stress      eps (Eq. 18, one-sided on boundary nodes) -> sigma_J = dC_JK eps_K (Eq. 11)
-//   k_div_fftx    q on the extended nodes [-1, n] (central-difference divergence of sigma plus
-//                 the density term), zero-padded to 2 n_x and FFT'd along x
-//   k_strided     forward FFT along y (zero padding pruned on load)
-//   k_fftz_green  forward FFT along z, u-hat_i = sum_j G-hat_ij q-hat_j, inverse FFT along z, crop
-//   k_strided     inverse FFT along y, crop
-//   k_fftx_out    inverse FFT along x, crop, Au = u - u_s
+//   k_divq        q on the extended nodes [-1, n] (central-difference divergence of sigma plus
+//                 the density term)
+//   k(4)_rows     q zero-padded to 2 n_x and FFT'd along x
+//   k(4)_strided  forward FFT along y (zero padding pruned on load)
+//   k(4)_fftz_green  forward FFT along z, u-hat_i = sum_j G-hat_ij q-hat_j, inverse FFT along z, crop
+//   k(4)_strided  inverse FFT along y, crop
+//   k(4)_fftx_out inverse FFT along x, crop, Au = u - u_s
+// Power-of-two line lengths 16..256 use the compile-time four-step FFT kernels (k4_*), any other
+// length the runtime mixed-radix Stockham kernels.
 // Only three displacement-like components pass through the FFTs: the derivative of the
 // Green tensor in Eq. 8 is applied as the central difference D_k in real space, which is
 // exactly the factor i sin(k h)/h of the spectral form.  The contrast source q is shifted by
 // one node (index p holds node p - 1) so that it occupies [0, n+2) of the 2n-periodic grid;
 // the result is then read at indices 1..n.  1/P of the inverse FFT is folded into G-hat.
+#include <mutex>
+#include <vector>
+
 #include "kernels.h"
 #include "fft.cuh"
+#include "fft4.cuh"
 
 namespace lsm {
 
 static constexpr int NTH = 256;
+
+// FFT engines.  GenericFFT: runtime mixed-radix Stockham plan, ping-pong buffers, any block size.
+// FourStepFFT<A, B>: compile-time L = A * B, in place, exactly NL * TPL threads per block.
+// Launch bounds of the FFT kernels.  Four-step tiles have at most 384 threads (FP32) or 192
+// (FP64); asking for two resident FP32 blocks keeps those kernels at <= 85 registers, while the
+// FP64 ones keep their 16-point DFTs in up to 255 registers without spilling.
+template <typename T, bool INPLACE> struct FftBounds {
+    static constexpr int threads = INPLACE ? (sizeof(T) == 8 ? 192 : 384) : 512;
+    static constexpr int blocks = (INPLACE && sizeof(T) == 4) ? 2 : 1;
+};
+#define LSM_COMMA ,
+#define LSM_FFT_BOUND(T, F) __launch_bounds__(FftBounds<T LSM_COMMA F::INPLACE>::threads, FftBounds<T LSM_COMMA F::INPLACE>::blocks)
+
+struct GenericFFT {
+    static constexpr bool INPLACE = false;
+    static constexpr int TPL = 0;
+    template <int S, typename C>
+    static __device__ __forceinline__ C* run(C* a, C* b, const FftPlan& p, int NL, int LD, const C* __restrict__ tw) {
+        return fft_smem<S>(a, b, p, NL, LD, tw, threadIdx.x, blockDim.x);
+    }
+};
+template <int A, int B>
+struct FourStepFFT {
+    static constexpr int A_ = A, B_ = B;
+    static constexpr bool INPLACE = true;
+    static constexpr int TPL = FourStep<A, B>::TPL;
+    template <int S, typename C>
+    static __device__ __forceinline__ C* run(C* a, C*, const FftPlan&, int NL, int LD, const C* __restrict__ tw) {
+        fft4_smem<A, B, S>(a, NL, LD, tw, threadIdx.x);
+        return a;
+    }
+};
 
 // Voigt index (order 11, 22, 33, 23, 13, 12) of the tensor pair (j, k).
 __device__ __forceinline__ int t2v(int j, int k) { return (j == k) ? j : (6 - j - k); }
@@ -104,69 +143,6 @@ __global__ void __launch_bounds__(NTH) k_stress(Dims d, const T* __restrict__ dC
 }
 
 // ---------------------------------------------------------------------------------------------
-// contrast source q (extended nodes) + forward FFT along x.  CTA: B rows y' at one z', 3 comps.
-// ---------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NTH) k_div_fftx(Dims d, const T* __restrict__ drho, const ApplySys<T>* __restrict__ sys,
-                                                  FftPlan px, const typename cplx_of<T>::type* __restrict__ tw, int B) {
-    typedef typename cplx_of<T>::type C;
-    extern __shared__ unsigned char smem_raw[];
-    const ApplySys<T> S = sys[blockIdx.z];
-    if (S.run && !*S.run) return;
-    const int NL = 3 * B, LD = NL + 1, L = d.Lx;
-    C* sa = reinterpret_cast<C*>(smem_raw);
-    C* sb = sa + (size_t)L * LD;
-    const int zp = blockIdx.y;            // extended z index; node z = zp - 1
-    const int y0 = blockIdx.x * B;
-    const long long N = d.N;
-    const long long sxy = (long long)d.nx * d.ny;
-    const C* __restrict__ sig = S.w1;
-    const C* __restrict__ u = S.u;
-    const T i2h = (T)(0.5 / d.h);
-    const int pz = zp - 1;
-    for (int i = threadIdx.x; i < NL * L; i += NTH) {
-        const int xp = i % L;
-        const int l = i / L;
-        const int j = l / B;
-        const int yp = y0 + (l % B);
-        C q = czero<C>();
-        if (xp < d.ex && yp < d.ey) {
-            const int p[3] = {xp - 1, yp - 1, pz};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const C* sJ = sig + (long long)t2v(j, k) * N;
-                int a[3] = {p[0], p[1], p[2]};
-                a[k] += 1;
-                if (a[0] >= 0 && a[0] < d.nx && a[1] >= 0 && a[1] < d.ny && a[2] >= 0 && a[2] < d.nz)
-                    q = cadd(q, sJ[a[2] * sxy + (long long)a[1] * d.nx + a[0]]);
-                a[k] -= 2;
-                if (a[0] >= 0 && a[0] < d.nx && a[1] >= 0 && a[1] < d.ny && a[2] >= 0 && a[2] < d.nz)
-                    q = csub(q, sJ[a[2] * sxy + (long long)a[1] * d.nx + a[0]]);
-            }
-            q = cscale(q, i2h);
-            if (p[0] >= 0 && p[0] < d.nx && p[1] >= 0 && p[1] < d.ny && p[2] >= 0 && p[2] < d.nz) {
-                const long long idx = p[2] * sxy + (long long)p[1] * d.nx + p[0];
-                const T w = S.omega2 * __ldg(&drho[idx]);
-                const C uj = u[j * N + idx];
-                q.x += w * uj.x;
-                q.y += w * uj.y;
-            }
-        }
-        sa[xp * LD + l] = q;
-    }
-    __syncthreads();
-    C* r = fft_smem<-1>(sa, sb, px, NL, LD, tw, threadIdx.x, NTH);
-    C* __restrict__ out = S.w2;  // [3][ez][ey][Lx]
-    for (int i = threadIdx.x; i < NL * L; i += NTH) {
-        const int kx = i % L;
-        const int l = i / L;
-        const int j = l / B;
-        const int yp = y0 + (l % B);
-        if (yp < d.ey) out[(((long long)j * d.ez + zp) * d.ey + yp) * L + kx] = r[kx * LD + l];
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
 // generic strided pass: TX consecutive lines (along x) of a strided axis.  Element e of line x of
 // outer (oy = blockIdx.y, comp c) lives at base + c*os2 + oy*os1 + e*es + x.
 // ---------------------------------------------------------------------------------------------
@@ -190,11 +166,11 @@ __device__ __forceinline__ C* pick(const ApplySys<typename real_of<C>::type>& S,
     }
 }
 
-template <int DIR, typename C>
+template <int DIR, class F, typename C>
 __device__ __forceinline__ void strided_tile(const C* src, C* dst, const FftPlan& p, const C* __restrict__ tw,
                                              const StridedArgs& a, int x0, C* sa, C* sb) {
     const int L = p.L, TX = a.TX;
-    for (int i = threadIdx.x; i < L * TX; i += NTH) {
+    for (int i = threadIdx.x; i < L * TX; i += blockDim.x) {
         const int l = i % TX;
         const int e = i / TX;
         const int x = x0 + l;
@@ -204,8 +180,8 @@ __device__ __forceinline__ void strided_tile(const C* src, C* dst, const FftPlan
         sa[i] = v;
     }
     __syncthreads();
-    C* r = fft_smem<DIR>(sa, sb, p, TX, TX, tw, threadIdx.x, NTH);
-    for (int i = threadIdx.x; i < a.out_count * TX; i += NTH) {
+    C* r = F::template run<DIR>(sa, sb, p, TX, TX, tw);
+    for (int i = threadIdx.x; i < a.out_count * TX; i += blockDim.x) {
         const int l = i % TX;
         const int eo = i / TX;
         const int x = x0 + l;
@@ -213,8 +189,8 @@ __device__ __forceinline__ void strided_tile(const C* src, C* dst, const FftPlan
     }
 }
 
-template <typename T, int DIR>
-__global__ void __launch_bounds__(NTH) k_strided(FftPlan p, const typename cplx_of<T>::type* __restrict__ tw,
+template <typename T, int DIR, class F>
+__global__ void LSM_FFT_BOUND(T, F) k_strided(FftPlan p, const typename cplx_of<T>::type* __restrict__ tw,
                                                  StridedArgs a, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ unsigned char smem_raw[];
@@ -223,10 +199,10 @@ __global__ void __launch_bounds__(NTH) k_strided(FftPlan p, const typename cplx_
     const ApplySys<T> S = sys[s];
     if (S.run && !*S.run) return;
     C* sa = reinterpret_cast<C*>(smem_raw);
-    C* sb = sa + (size_t)p.L * a.TX;
+    C* sb = F::INPLACE ? sa : sa + (size_t)p.L * a.TX;
     const C* src = pick<C>(S, a.src_sel) + c * a.src_os2 + blockIdx.y * a.src_os1;
     C* dst = pick<C>(S, a.dst_sel) + c * a.dst_os2 + blockIdx.y * a.dst_os1;
-    strided_tile<DIR>(src, dst, p, tw, a, blockIdx.x * a.TX, sa, sb);
+    strided_tile<DIR, F>(src, dst, p, tw, a, blockIdx.x * a.TX, sa, sb);
 }
 
 // raw-pointer variant for the Green spectrum setup (in place allowed: each CTA owns its tile)
@@ -240,7 +216,130 @@ __global__ void __launch_bounds__(NTH) k_strided_raw(FftPlan p, const typename c
     C* sb = sa + (size_t)p.L * a.TX;
     const C* src = src0 + blockIdx.z * a.src_os2 + blockIdx.y * a.src_os1;
     C* dst = dst0 + blockIdx.z * a.dst_os2 + blockIdx.y * a.dst_os1;
-    strided_tile<DIR>(src, dst, p, tw, a, blockIdx.x * a.TX, sa, sb);
+    strided_tile<DIR, GenericFFT>(src, dst, p, tw, a, blockIdx.x * a.TX, sa, sb);
+}
+
+// four-step strided pass: step 1 loads straight from global memory, the last step stores straight
+// to global memory; one shared-memory exchange in between.  Block = TX * TPL threads.
+template <typename T, int DIR, int A, int B>
+__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const typename cplx_of<T>::type* __restrict__ tw,
+                                                                     StridedArgs a, const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ unsigned char smem_raw[];
+    const int c = blockIdx.z % a.ncomp;
+    const int sidx = blockIdx.z / a.ncomp;
+    const ApplySys<T> S = sys[sidx];
+    if (S.run && !*S.run) return;
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const C* __restrict__ src = pick<C>(S, a.src_sel) + c * a.src_os2 + blockIdx.y * a.src_os1;
+    C* __restrict__ dst = pick<C>(S, a.dst_sel) + c * a.dst_os2 + blockIdx.y * a.dst_os1;
+    const int x0 = blockIdx.x * a.TX;
+    const int TX = a.TX;
+    auto ld = [&](int l, int e) -> C {
+        const int x = x0 + l, es = e - a.in_off;
+        return (x < a.nlines && es >= 0 && es < a.in_count) ? src[es * a.src_es + x] : czero<C>();
+    };
+    auto st = [&](int l, int k, C v) {
+        const int x = x0 + l, eo = k - a.out_off;
+        if (x < a.nlines && eo >= 0 && eo < a.out_count) dst[eo * a.dst_es + x] = v;
+    };
+    fft4_io<A, B, DIR, false, false>(s, TX, TX, tw, threadIdx.x, ld, st);
+}
+
+// four-step z pass with the Green multiply.  Block = 3 TX * TPL threads; line l = c * TX + lx.
+// One block serves one (kx tile, ky) column for every system of the batch in turn.  Its slice of
+// the octant spectrum (|kz| = 0..nz, 6 components, TX values of kx at one ky) is copied to shared
+// memory asynchronously, once for all consecutive systems that share the spectrum (the sources
+// of one frequency), while the first of them runs its forward FFT.
+template <typename T, bool CONJ, int A, int B>
+__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftz_green(Dims d, const typename cplx_of<T>::type* __restrict__ tw,
+                                                                        const ApplySys<T>* __restrict__ sys, int nsys, int TX,
+                                                                        int in_count, int in_off, int out_count, int out_off,
+                                                                        int src_sel, int dst_sel) {
+    typedef typename cplx_of<T>::type C;
+    typedef typename real_of<C>::type R;
+    extern __shared__ unsigned char smem_raw[];
+    const int NL = 3 * TX;
+    const int L = d.Lz;
+    C* s = reinterpret_cast<C*>(smem_raw);
+    C* sG = s + (size_t)L * NL;   // [nz + 1][6][TX]
+    const int ky = blockIdx.y;
+    const int x0 = blockIdx.x * TX;
+    const int fy = ky <= d.ny ? ky : d.Ly - ky;
+    const R sy = ky > d.ny ? (R)-1 : (R)1;
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long plane = (long long)d.Ly * d.Lx;
+    const long long s_c = (long long)in_count * plane, d_c = (long long)out_count * plane;
+    const long long off = (long long)ky * d.Lx + x0;
+    const C* staged = nullptr;
+    for (int si = 0; si < nsys; ++si) {
+        const ApplySys<T> S = sys[si];
+        if (S.run && !*S.run) continue;
+        const bool fresh = S.ghat != staged;
+        if (fresh) {
+            __syncthreads();  // the previous system's multiply has finished with the old slice
+            const int nf = d.nz + 1;
+            for (int i = threadIdx.x; i < nf * 6 * TX; i += blockDim.x) {
+                const int lx = i % TX;
+                const int r = i / TX;
+                const int c = r % 6;
+                const int fz = r / 6;
+                const int kx = x0 + lx;
+                if (kx < d.Lx) {
+                    const int fx = kx <= d.nx ? kx : d.Lx - kx;
+                    cp_async_elem(&sG[i], S.ghat + c * NO + ((long long)fz * (d.ny + 1) + fy) * (d.nx + 1) + fx);
+                }
+            }
+            cp_async_commit();
+            staged = S.ghat;
+        }
+        const C* __restrict__ src = pick<C>(S, src_sel);
+        C* __restrict__ dst = pick<C>(S, dst_sel);
+        auto ld_g = [&](int l, int e) -> C {
+            const int c = l / TX, lx = l - c * TX, es = e - in_off;
+            return (x0 + lx < d.Lx && es >= 0 && es < in_count) ? src[c * s_c + es * plane + off + lx] : czero<C>();
+        };
+        auto st_s = [&](int l, int k, C v) { s[k * NL + l] = v; };
+        fft4_io<A, B, -1, false, true>(s, NL, NL, tw, threadIdx.x, ld_g, st_s);
+        if (fresh) {
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < L * TX; i += blockDim.x) {
+            const int lx = i % TX;
+            const int kz = i / TX;
+            const int kx = x0 + lx;
+            if (kx >= d.Lx) continue;
+            const int fz = kz <= d.nz ? kz : L - kz;
+            const R sz = kz > d.nz ? (R)-1 : (R)1;
+            const R sx = kx > d.nx ? (R)-1 : (R)1;
+            const C* g = sG + fz * 6 * TX + lx;
+            C G[6];
+            G[0] = g[0];
+            G[1] = g[TX];
+            G[2] = g[2 * TX];
+            G[3] = cscale(g[3 * TX], sy * sz);
+            G[4] = cscale(g[4 * TX], sx * sz);
+            G[5] = cscale(g[5 * TX], sx * sy);
+            if (CONJ) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) G[c] = cconj(G[c]);
+            }
+            C* row = s + kz * NL + lx;
+            const C q0 = row[0], q1 = row[TX], q2 = row[2 * TX];
+            row[0] = cadd(cadd(cmul(G[0], q0), cmul(G[5], q1)), cmul(G[4], q2));
+            row[TX] = cadd(cadd(cmul(G[5], q0), cmul(G[1], q1)), cmul(G[3], q2));
+            row[2 * TX] = cadd(cadd(cmul(G[4], q0), cmul(G[3], q1)), cmul(G[2], q2));
+        }
+        __syncthreads();
+        auto ld_s = [&](int l, int e) -> C { return s[e * NL + l]; };
+        auto st_g = [&](int l, int k, C v) {
+            const int c = l / TX, lx = l - c * TX, eo = k - out_off;
+            if (x0 + lx < d.Lx && eo >= 0 && eo < out_count) dst[c * d_c + eo * plane + off + lx] = v;
+        };
+        fft4_io<A, B, 1, true, false>(s, NL, NL, tw, threadIdx.x, ld_s, st_g);
+        __syncthreads();  // the next system's forward step writes s
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -248,8 +347,8 @@ __global__ void __launch_bounds__(NTH) k_strided_raw(FftPlan p, const typename c
 // adjoint), inverse z FFT.  CTA: TX lines along x at one ky, all three components.
 // src [3][in_count][Ly][Lx] (sel), dst [3][out_count][Ly][Lx] (sel)
 // ---------------------------------------------------------------------------------------------
-template <typename T, bool CONJ>
-__global__ void __launch_bounds__(NTH) k_fftz_green(Dims d, FftPlan pz, const typename cplx_of<T>::type* __restrict__ tw,
+template <typename T, bool CONJ, class F>
+__global__ void LSM_FFT_BOUND(T, F) k_fftz_green(Dims d, FftPlan pz, const typename cplx_of<T>::type* __restrict__ tw,
                                                     const ApplySys<T>* __restrict__ sys, int TX, int in_count, int in_off,
                                                     int out_count, int out_off, int src_sel, int dst_sel) {
     typedef typename cplx_of<T>::type C;
@@ -258,14 +357,14 @@ __global__ void __launch_bounds__(NTH) k_fftz_green(Dims d, FftPlan pz, const ty
     if (S.run && !*S.run) return;
     const int L = d.Lz, NL = 3 * TX;
     C* sa = reinterpret_cast<C*>(smem_raw);
-    C* sb = sa + (size_t)L * NL;
+    C* sb = F::INPLACE ? sa : sa + (size_t)L * NL;
     const int ky = blockIdx.y;
     const int x0 = blockIdx.x * TX;
     const long long plane = (long long)d.Ly * d.Lx;
     const C* src = pick<C>(S, src_sel);
     C* dst = pick<C>(S, dst_sel);
     const long long s_c = (long long)in_count * plane, d_c = (long long)out_count * plane;
-    for (int i = threadIdx.x; i < L * NL; i += NTH) {
+    for (int i = threadIdx.x; i < L * NL; i += blockDim.x) {
         const int lx = i % TX;
         const int rest = i / TX;
         const int c = rest % 3;
@@ -277,9 +376,9 @@ __global__ void __launch_bounds__(NTH) k_fftz_green(Dims d, FftPlan pz, const ty
         sa[e * NL + c * TX + lx] = v;
     }
     __syncthreads();
-    C* r = fft_smem<-1>(sa, sb, pz, NL, NL, tw, threadIdx.x, NTH);
+    C* r = F::template run<-1>(sa, sb, pz, NL, NL, tw);
     C* o = (r == sa) ? sb : sa;
-    for (int i = threadIdx.x; i < L * TX; i += NTH) {
+    for (int i = threadIdx.x; i < L * TX; i += blockDim.x) {
         const int lx = i % TX;
         const int kz = i / TX;
         const int kx = x0 + lx;
@@ -293,8 +392,8 @@ __global__ void __launch_bounds__(NTH) k_fftz_green(Dims d, FftPlan pz, const ty
         row[2 * TX] = cadd(cadd(cmul(G[4], q0), cmul(G[3], q1)), cmul(G[2], q2));
     }
     __syncthreads();
-    C* r2 = fft_smem<1>(r, o, pz, NL, NL, tw, threadIdx.x, NTH);
-    for (int i = threadIdx.x; i < out_count * NL; i += NTH) {
+    C* r2 = F::template run<1>(r, o, pz, NL, NL, tw);
+    for (int i = threadIdx.x; i < out_count * NL; i += blockDim.x) {
         const int lx = i % TX;
         const int rest = i / TX;
         const int c = rest % 3;
@@ -307,8 +406,8 @@ __global__ void __launch_bounds__(NTH) k_fftz_green(Dims d, FftPlan pz, const ty
 // ---------------------------------------------------------------------------------------------
 // inverse FFT along x + crop + Au = u - u_s.  CTA: B rows y at one z, 3 comps.  src w1 [3][nz][ny][Lx]
 // ---------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NTH) k_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys, FftPlan px,
+template <typename T, class F>
+__global__ void LSM_FFT_BOUND(T, F) k_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys, FftPlan px,
                                                   const typename cplx_of<T>::type* __restrict__ tw, int B) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ unsigned char smem_raw[];
@@ -316,11 +415,11 @@ __global__ void __launch_bounds__(NTH) k_fftx_out(Dims d, const ApplySys<T>* __r
     if (S.run && !*S.run) return;
     const int NL = 3 * B, LD = NL + 1, L = d.Lx;
     C* sa = reinterpret_cast<C*>(smem_raw);
-    C* sb = sa + (size_t)L * LD;
+    C* sb = F::INPLACE ? sa : sa + (size_t)L * LD;
     const int z = blockIdx.y;
     const int y0 = blockIdx.x * B;
-    const C* __restrict__ src = S.w1;
-    for (int i = threadIdx.x; i < NL * L; i += NTH) {
+    const C* __restrict__ src = S.w2;
+    for (int i = threadIdx.x; i < NL * L; i += blockDim.x) {
         const int kx = i % L;
         const int l = i / L;
         const int c = l / B;
@@ -330,8 +429,8 @@ __global__ void __launch_bounds__(NTH) k_fftx_out(Dims d, const ApplySys<T>* __r
         sa[kx * LD + l] = v;
     }
     __syncthreads();
-    C* r = fft_smem<1>(sa, sb, px, NL, LD, tw, threadIdx.x, NTH);
-    for (int i = threadIdx.x; i < NL * d.nx; i += NTH) {
+    C* r = F::template run<1>(sa, sb, px, NL, LD, tw);
+    for (int i = threadIdx.x; i < NL * d.nx; i += blockDim.x) {
         const int x = i % d.nx;
         const int l = i / d.nx;
         const int c = l / B;
@@ -339,6 +438,144 @@ __global__ void __launch_bounds__(NTH) k_fftx_out(Dims d, const ApplySys<T>* __r
         if (y < d.ny) {
             const long long idx = (((long long)c * d.nz + z) * d.ny + y) * d.nx + x;
             S.out[idx] = csub(S.u[idx], r[(x + 1) * LD + l]);
+        }
+    }
+    if (S.count && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(S.count, 1ull);
+}
+
+// ---------------------------------------------------------------------------------------------
+// contrast source on the extended nodes: q_j = sum_k D_k sigma_jk + w^2 drho u_j, q [3][ez][ey][ex]
+// (index p holds node p - 1).  sigma in w1, q written to w2.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) k_divq(Dims d, const T* __restrict__ drho, const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    const C* __restrict__ sig = S.w1;
+    const C* __restrict__ u = S.u;
+    C* __restrict__ q = S.w2;
+    const long long N = d.N;
+    const long long E = (long long)d.ex * d.ey * d.ez;
+    const long long sxy = (long long)d.nx * d.ny;
+    const T i2h = (T)(0.5 / d.h);
+    for (long long idx = (long long)blockIdx.x * NTH + threadIdx.x; idx < E; idx += (long long)gridDim.x * NTH) {
+        const int p0 = (int)(idx % d.ex) - 1;
+        const int p1 = (int)((idx / d.ex) % d.ey) - 1;
+        const int p2 = (int)(idx / ((long long)d.ex * d.ey)) - 1;
+        const int p[3] = {p0, p1, p2};
+        const int nn[3] = {d.nx, d.ny, d.nz};
+        const long long st[3] = {1, (long long)d.nx, sxy};
+        const bool in0 = p0 >= 0 && p0 < d.nx, in1 = p1 >= 0 && p1 < d.ny, in2 = p2 >= 0 && p2 < d.nz;
+        const long long base = (long long)p2 * sxy + (long long)p1 * d.nx + p0;
+        C qj[3] = {czero<C>(), czero<C>(), czero<C>()};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // the neighbours p +- e_k are model nodes when the other two coordinates are inside
+            // and p_k + 1 (resp. p_k - 1) is inside along k
+            const bool other = (k == 0 ? (in1 && in2) : (k == 1 ? (in0 && in2) : (in0 && in1)));
+            if (!other) continue;
+            const bool hi = p[k] + 1 >= 0 && p[k] + 1 < nn[k];
+            const bool lo = p[k] - 1 >= 0 && p[k] - 1 < nn[k];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const C* sJ = sig + (long long)t2v(j, k) * N + base;
+                if (hi) qj[j] = cadd(qj[j], sJ[st[k]]);
+                if (lo) qj[j] = csub(qj[j], sJ[-st[k]]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) qj[j] = cscale(qj[j], i2h);
+        if (in0 && in1 && in2) {
+            const T w = S.omega2 * __ldg(&drho[base]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const C uj = u[j * N + base];
+                qj[j].x += w * uj.x;
+                qj[j].y += w * uj.y;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) q[j * E + idx] = qj[j];
+    }
+}
+
+// four-step contiguous-rows FFT: NL rows per block, compile-time sizes, loads batched in registers.
+// Row r of src starts at src + r * in_count (placed at in_off), row r of dst at dst + r * out_count.
+template <typename T, int DIR, int A, int B, int NL>
+__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_rows(const typename cplx_of<T>::type* __restrict__ tw,
+                                                                  const ApplySys<T>* __restrict__ sys, int src_sel, int dst_sel,
+                                                                  long long nrows, int in_count, int in_off, int out_count,
+                                                                  int out_off) {
+    typedef typename cplx_of<T>::type C;
+    constexpr int L = A * B, TPL = FourStep<A, B>::TPL, NTHR = NL * TPL, LD = NL + 1, PER = L / TPL;
+    extern __shared__ unsigned char smem_raw[];
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const C* __restrict__ src = pick<C>(S, src_sel);
+    C* __restrict__ dst = pick<C>(S, dst_sel);
+    const long long r0 = (long long)blockIdx.x * NL;
+    const int tid = threadIdx.x;
+    C v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NTHR;
+        const int e = i % L, l = i / L;
+        const long long row = r0 + l;
+        const int es = e - in_off;
+        v[k] = (row < nrows && es >= 0 && es < in_count) ? src[row * in_count + es] : czero<C>();
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NTHR;
+        s[(i % L) * LD + i / L] = v[k];
+    }
+    __syncthreads();
+    fft4_smem<A, B, DIR>(s, NL, LD, tw, tid);
+    for (int i = tid; i < NL * out_count; i += NTHR) {
+        const int e = i % out_count, l = i / out_count;
+        const long long row = r0 + l;
+        if (row < nrows) dst[row * out_count + e] = s[(e + out_off) * LD + l];
+    }
+}
+
+// four-step inverse x FFT + crop + Au = u - u_s; ROWS rows x 3 components per block; src w2.
+template <typename T, int A, int B, int ROWS>
+__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys,
+                                                                      const typename cplx_of<T>::type* __restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    constexpr int L = A * B, TPL = FourStep<A, B>::TPL, NL = 3 * ROWS, NTHR = NL * TPL, LD = NL + 1, PER = L / TPL;
+    extern __shared__ unsigned char smem_raw[];
+    const ApplySys<T> S = sys[blockIdx.z];
+    if (S.run && !*S.run) return;
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int z = blockIdx.y;
+    const int y0 = blockIdx.x * ROWS;
+    const C* __restrict__ src = S.w2;
+    const int tid = threadIdx.x;
+    C v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NTHR;
+        const int kx = i % L, l = i / L;
+        const int c = l / ROWS, y = y0 + l % ROWS;
+        v[k] = (y < d.ny) ? src[(((long long)c * d.nz + z) * d.ny + y) * L + kx] : czero<C>();
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NTHR;
+        s[(i % L) * LD + i / L] = v[k];
+    }
+    __syncthreads();
+    fft4_smem<A, B, 1>(s, NL, LD, tw, tid);
+    const int nx = d.nx;
+    for (int i = tid; i < NL * nx; i += NTHR) {
+        const int x = i % nx, l = i / nx;
+        const int c = l / ROWS, y = y0 + l % ROWS;
+        if (y < d.ny) {
+            const long long idx = (((long long)c * d.nz + z) * d.ny + y) * nx + x;
+            S.out[idx] = csub(S.u[idx], s[(x + 1) * LD + l]);
         }
     }
     if (S.count && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(S.count, 1ull);
@@ -504,24 +741,19 @@ __global__ void __launch_bounds__(NTH) k_adj_out(Dims d, const T* __restrict__ d
 // host launchers
 // ---------------------------------------------------------------------------------------------
 void apply_ws_elems(const Dims& d, long long* w1, long long* w2) {
-    const long long N = d.N;
-    const long long sig = 6 * N;
-    const long long y1 = 3LL * d.ez * d.Ly * d.Lx;
-    const long long y2 = 3LL * d.nz * d.ny * d.Lx;
-    const long long adjz = 3LL * d.ez * d.ey * d.ex;
-    const long long adjw1a = 3LL * d.nz * d.ny * d.Lx;
-    long long a = sig > y1 ? sig : y1;
-    a = a > y2 ? a : y2;
-    a = a > adjz ? a : adjz;
-    a = a > adjw1a ? a : adjw1a;
-    const long long x1 = 3LL * d.ez * d.ey * d.Lx;
-    const long long z1 = 3LL * d.nz * d.Ly * d.Lx;
-    const long long adjw2 = 3LL * d.ez * d.ey * d.Lx;
-    long long b = x1 > z1 ? x1 : z1;
-    b = b > sig ? b : sig;
-    b = b > adjw2 ? b : adjw2;
-    *w1 = a;
-    *w2 = b;
+    // both buffers hold any intermediate of the apply or the adjoint
+    const long long c[] = {
+        6 * d.N,                           // sigma
+        3LL * d.ex * d.ey * d.ez,          // q / z on the extended nodes
+        3LL * d.ez * d.ey * d.Lx,          // after the x FFT
+        3LL * d.ez * d.Ly * d.Lx,          // after the y FFT
+        3LL * d.nz * d.Ly * d.Lx,          // after the z pass
+        3LL * d.nz * d.ny * d.Lx,          // after the inverse y FFT / first adjoint pass
+    };
+    long long m = 0;
+    for (long long v : c) m = v > m ? v : m;
+    *w1 = m;
+    *w2 = m;
 }
 
 static const size_t SMEM_CAP = 96 * 1024;
@@ -558,73 +790,194 @@ static inline int grid_elems(long long n) {
     return (int)b;
 }
 
+// First use of a kernel: prefer the largest shared-memory carveout (several FFT tiles per SM),
+// and raise its dynamic shared-memory limit whenever a launch needs more than 48 KB.
+static void smem_attr(const void* k, size_t sm) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> seen;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : seen)
+        if (e.first == k) {
+            if (e.second >= sm) return;
+            if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            e.second = sm;
+            return;
+        }
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    seen.push_back({k, sm});
+}
+
+// Call fn with the FFT engine for line length L: compile-time four-step for 16..256, else generic.
+template <typename Fn>
+static void with_engine(int L, Fn&& fn) {
+    switch (L) {
+        case 16: fn(FourStepFFT<4, 4>()); break;
+        case 32: fn(FourStepFFT<4, 8>()); break;
+        case 64: fn(FourStepFFT<8, 8>()); break;
+        case 128: fn(FourStepFFT<8, 16>()); break;
+        case 256: fn(FourStepFFT<16, 16>()); break;
+        default: fn(GenericFFT()); break;
+    }
+}
+
+// tile of B rows x 3 components for the contiguous x passes
+template <typename T, class F>
+static void rows_cfg(int L, int& B, int& threads, size_t& sm) {
+    typedef typename cplx_of<T>::type C;
+    if constexpr (F::INPLACE) {
+        B = sizeof(T) == 4 ? 8 : 4;
+        threads = 3 * B * F::TPL;
+        sm = (size_t)L * (3 * B + 1) * sizeof(C);
+    } else {
+        B = rows_per_tile<T>(L);
+        threads = NTH;
+        sm = 2 * (size_t)L * (3 * B + 1) * sizeof(C);
+    }
+}
+// tile of TX consecutive lines x ncomp components for the strided passes
+template <typename T, class F>
+static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm) {
+    typedef typename cplx_of<T>::type C;
+    if constexpr (F::INPLACE) {
+        TX = sizeof(T) == 4 ? (ncomp == 1 ? 16 : 8) : (ncomp == 1 ? 8 : 4);
+        threads = ncomp * TX * F::TPL;
+        sm = (size_t)L * ncomp * TX * sizeof(C);
+    } else {
+        TX = strided_tx<T>(L, ncomp);
+        threads = NTH;
+        sm = 2 * (size_t)L * ncomp * TX * sizeof(C);
+    }
+}
+
+// forward x FFT of the contrast source rows: w2 [3][ez][ey][ex] -> w1 [3][ez][ey][Lx]
+template <typename T>
+static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, cudaStream_t st) {
+    typedef typename cplx_of<T>::type C;
+    const long long nrows = 3LL * d.ez * d.ey;
+    with_engine(d.Lx, [&](auto eng) {
+        using F = decltype(eng);
+        if constexpr (F::INPLACE) {
+            constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 24 : 12;
+            const size_t sm = (size_t)A * B * (NL + 1) * sizeof(C);
+            smem_attr((const void*)k4_rows<T, -1, A, B, NL>, sm);
+            k4_rows<T, -1, A, B, NL><<<dim3(cdiv(nrows, NL), nsys), NL * F::TPL, sm, st>>>(
+                (const C*)pl.twx, sys, 3, 2, nrows, d.ex, 0, d.Lx, 0);
+        } else {
+            const int NL = generic_rows_nl<T>(d.Lx);
+            const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+            smem_attr((const void*)k_rows<T, -1>, sm);
+            k_rows<T, -1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, (const C*)pl.twx, sys, 3, 2, nrows, NL,
+                                                                         d.ex, 0, d.Lx, 0);
+        }
+    });
+}
+
+template <typename T>
+static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, cudaStream_t st) {
+    typedef typename cplx_of<T>::type C;
+    with_engine(d.Lx, [&](auto eng) {
+        using F = decltype(eng);
+        if constexpr (F::INPLACE) {
+            constexpr int A = F::A_, B = F::B_, ROWS = sizeof(T) == 4 ? 8 : 4;
+            const size_t sm = (size_t)A * B * (3 * ROWS + 1) * sizeof(C);
+            smem_attr((const void*)k4_fftx_out<T, A, B, ROWS>, sm);
+            k4_fftx_out<T, A, B, ROWS><<<dim3(cdiv(d.ny, ROWS), d.nz, nsys), 3 * ROWS * F::TPL, sm, st>>>(
+                d, sys, (const C*)pl.twx);
+        } else {
+            int B, th;
+            size_t sm;
+            rows_cfg<T, F>(d.Lx, B, th, sm);
+            smem_attr((const void*)k_fftx_out<T, F>, sm);
+            k_fftx_out<T, F><<<dim3(cdiv(d.ny, B), d.nz, nsys), th, sm, st>>>(d, sys, pl.px, (const C*)pl.twx, B);
+        }
+    });
+}
+
+// y pass over `planes` planes: src [3][planes][in_count][Lx] (sel) -> dst [3][planes][out_count][Lx] (sel)
+template <typename T, int DIR>
+static void launch_ypass(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int planes, int in_count,
+                         int in_off, int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st) {
+    typedef typename cplx_of<T>::type C;
+    with_engine(d.Ly, [&](auto eng) {
+        using F = decltype(eng);
+        StridedArgs a;
+        int th;
+        size_t sm;
+        strided_cfg<T, F>(d.Ly, 1, a.TX, th, sm);
+        a.nlines = d.Lx;
+        a.in_count = in_count; a.in_off = in_off; a.out_count = out_count; a.out_off = out_off;
+        a.src_es = d.Lx; a.src_os1 = (long long)in_count * d.Lx; a.src_os2 = (long long)planes * in_count * d.Lx;
+        a.dst_es = d.Lx; a.dst_os1 = (long long)out_count * d.Lx; a.dst_os2 = (long long)planes * out_count * d.Lx;
+        a.ncomp = 3; a.src_sel = src_sel; a.dst_sel = dst_sel;
+        if constexpr (F::INPLACE) {
+            constexpr int A = F::A_, B = F::B_;
+            smem_attr((const void*)k4_strided<T, DIR, A, B>, sm);
+            k4_strided<T, DIR, A, B><<<dim3(cdiv(d.Lx, a.TX), planes, 3 * nsys), th, sm, st>>>((const C*)pl.twy, a, sys);
+        } else {
+            smem_attr((const void*)k_strided<T, DIR, F>, sm);
+            k_strided<T, DIR, F><<<dim3(cdiv(d.Lx, a.TX), planes, 3 * nsys), th, sm, st>>>(pl.py, (const C*)pl.twy, a, sys);
+        }
+    });
+}
+
+template <typename T, bool CONJ>
+static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int in_count, int in_off,
+                         int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st) {
+    typedef typename cplx_of<T>::type C;
+    with_engine(d.Lz, [&](auto eng) {
+        using F = decltype(eng);
+        int TX, th;
+        size_t sm;
+        strided_cfg<T, F>(d.Lz, 3, TX, th, sm);
+        if constexpr (F::INPLACE) sm += (size_t)(d.nz + 1) * 6 * TX * sizeof(C);  // spectrum slice
+        if constexpr (F::INPLACE) {
+            constexpr int A = F::A_, B = F::B_;
+            smem_attr((const void*)k4_fftz_green<T, CONJ, A, B>, sm);
+            k4_fftz_green<T, CONJ, A, B><<<dim3(cdiv(d.Lx, TX), d.Ly, 1), th, sm, st>>>(
+                d, (const C*)pl.twz, sys, nsys, TX, in_count, in_off, out_count, out_off, src_sel, dst_sel);
+        } else {
+            smem_attr((const void*)k_fftz_green<T, CONJ, F>, sm);
+            k_fftz_green<T, CONJ, F><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), th, sm, st>>>(
+                d, pl.pz, (const C*)pl.twz, sys, TX, in_count, in_off, out_count, out_off, src_sel, dst_sel);
+        }
+    });
+}
+
 template <typename T>
 cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
                          long long* nl) {
-    typedef typename cplx_of<T>::type C;
     const Dims& d = m.d;
     const T* dC = (const T*)m.dC;
     const T* drho = (const T*)m.drho;
-    const C* twx = (const C*)pl.twx;
-    const C* twy = (const C*)pl.twy;
-    const C* twz = (const C*)pl.twz;
     KTimer* tm = m.timer;
     const bool f32 = sizeof(T) == 4;
-    // 1. strain + contraction
+    // 1. strain + contraction -> w1 [6][N]
     ktimer_mark(tm, 0, f32, st, 0);
     k_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
     ktimer_mark(tm, 0, f32, st, 1);
-    // 2. contrast source + forward x FFT -> w2 [3][ez][ey][Lx]
-    {
-        const int B = rows_per_tile<T>(d.Lx);
-        const size_t sm = 2 * (size_t)d.Lx * (3 * B + 1) * sizeof(C);
-        ktimer_mark(tm, 1, f32, st, 0);
-        k_div_fftx<T><<<dim3(cdiv(d.ey, B), d.ez, nsys), NTH, sm, st>>>(d, drho, sys, pl.px, twx, B);
-        ktimer_mark(tm, 1, f32, st, 1);
-    }
-    // 3. forward y FFT: w2 [3][ez][ey][Lx] -> w1 [3][ez][Ly][Lx]
-    {
-        StridedArgs a;
-        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
-        a.in_count = d.ey; a.in_off = 0; a.out_count = d.Ly; a.out_off = 0;
-        a.src_es = d.Lx; a.src_os1 = (long long)d.ey * d.Lx; a.src_os2 = (long long)d.ez * d.ey * d.Lx;
-        a.dst_es = d.Lx; a.dst_os1 = (long long)d.Ly * d.Lx; a.dst_os2 = (long long)d.ez * d.Ly * d.Lx;
-        a.ncomp = 3; a.src_sel = 3; a.dst_sel = 2;
-        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
-        ktimer_mark(tm, 2, f32, st, 0);
-        k_strided<T, -1><<<dim3(cdiv(d.Lx, a.TX), d.ez, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
-        ktimer_mark(tm, 2, f32, st, 1);
-    }
-    // 4. z FFT, Green multiply, inverse z FFT, crop: w1 [3][ez][Ly][Lx] -> w2 [3][nz][Ly][Lx]
-    {
-        const int TX = strided_tx<T>(d.Lz, 3);
-        const size_t sm = 2 * (size_t)d.Lz * 3 * TX * sizeof(C);
-        ktimer_mark(tm, 3, f32, st, 0);
-        k_fftz_green<T, false><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), NTH, sm, st>>>(d, pl.pz, twz, sys, TX, d.ez, 0, d.nz, 1, 2, 3);
-        ktimer_mark(tm, 3, f32, st, 1);
-    }
-    // 5. inverse y FFT + crop: w2 [3][nz][Ly][Lx] -> w1 [3][nz][ny][Lx]
-    {
-        StridedArgs a;
-        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
-        a.in_count = d.Ly; a.in_off = 0; a.out_count = d.ny; a.out_off = 1;
-        a.src_es = d.Lx; a.src_os1 = (long long)d.Ly * d.Lx; a.src_os2 = (long long)d.nz * d.Ly * d.Lx;
-        a.dst_es = d.Lx; a.dst_os1 = (long long)d.ny * d.Lx; a.dst_os2 = (long long)d.nz * d.ny * d.Lx;
-        a.ncomp = 3; a.src_sel = 3; a.dst_sel = 2;
-        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
-        ktimer_mark(tm, 4, f32, st, 0);
-        k_strided<T, 1><<<dim3(cdiv(d.Lx, a.TX), d.nz, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
-        ktimer_mark(tm, 4, f32, st, 1);
-    }
-    // 6. inverse x FFT + crop + Au = u - u_s
-    {
-        const int B = rows_per_tile<T>(d.Lx);
-        const size_t sm = 2 * (size_t)d.Lx * (3 * B + 1) * sizeof(C);
-        ktimer_mark(tm, 5, f32, st, 0);
-        k_fftx_out<T><<<dim3(cdiv(d.ny, B), d.nz, nsys), NTH, sm, st>>>(d, sys, pl.px, twx, B);
-        ktimer_mark(tm, 5, f32, st, 1);
-    }
-    if (nl) *nl += 6;
+    // 2. contrast source on the extended nodes -> w2 [3][ez][ey][ex]; forward x FFT -> w1 [3][ez][ey][Lx]
+    ktimer_mark(tm, 1, f32, st, 0);
+    k_divq<T><<<dim3(grid_elems((long long)d.ex * d.ey * d.ez), nsys), NTH, 0, st>>>(d, drho, sys);
+    launch_xfwd<T>(d, sys, nsys, pl, st);
+    ktimer_mark(tm, 1, f32, st, 1);
+    // 3. forward y FFT: w1 [3][ez][ey][Lx] -> w2 [3][ez][Ly][Lx]
+    ktimer_mark(tm, 2, f32, st, 0);
+    launch_ypass<T, -1>(d, sys, nsys, pl, d.ez, d.ey, 0, d.Ly, 0, 2, 3, st);
+    ktimer_mark(tm, 2, f32, st, 1);
+    // 4. z FFT, Green multiply, inverse z FFT, crop: w2 [3][ez][Ly][Lx] -> w1 [3][nz][Ly][Lx]
+    ktimer_mark(tm, 3, f32, st, 0);
+    launch_zpass<T, false>(d, sys, nsys, pl, d.ez, 0, d.nz, 1, 3, 2, st);
+    ktimer_mark(tm, 3, f32, st, 1);
+    // 5. inverse y FFT + crop: w1 [3][nz][Ly][Lx] -> w2 [3][nz][ny][Lx]
+    ktimer_mark(tm, 4, f32, st, 0);
+    launch_ypass<T, 1>(d, sys, nsys, pl, d.nz, d.Ly, 0, d.ny, 1, 2, 3, st);
+    ktimer_mark(tm, 4, f32, st, 1);
+    // 6. inverse x FFT + crop + Au = u - u_s (reads w2)
+    ktimer_mark(tm, 5, f32, st, 0);
+    launch_fftx_out<T>(d, sys, nsys, pl, st);
+    ktimer_mark(tm, 5, f32, st, 1);
+    if (nl) *nl += 7;
     return cudaGetLastError();
 }
 
@@ -636,48 +989,26 @@ cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* 
     const T* dC = (const T*)m.dC;
     const T* drho = (const T*)m.drho;
     const C* twx = (const C*)pl.twx;
-    const C* twy = (const C*)pl.twy;
-    const C* twz = (const C*)pl.twz;
     // 1. w placed at x positions 1..nx, forward x FFT: u [3][nz][ny][nx] -> w1 [3][nz][ny][Lx]
     {
         const int NL = generic_rows_nl<T>(d.Lx);
         const long long nrows = 3LL * d.nz * d.ny;
         const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+        smem_attr((const void*)k_rows<T, -1>, sm);
         k_rows<T, -1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, twx, sys, 0, 2, nrows, NL, d.nx, 1, d.Lx, 0);
     }
     // 2. forward y FFT, input at 1..ny: w1 [3][nz][ny][Lx] -> w2 [3][nz][Ly][Lx]
-    {
-        StridedArgs a;
-        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
-        a.in_count = d.ny; a.in_off = 1; a.out_count = d.Ly; a.out_off = 0;
-        a.src_es = d.Lx; a.src_os1 = (long long)d.ny * d.Lx; a.src_os2 = (long long)d.nz * d.ny * d.Lx;
-        a.dst_es = d.Lx; a.dst_os1 = (long long)d.Ly * d.Lx; a.dst_os2 = (long long)d.nz * d.Ly * d.Lx;
-        a.ncomp = 3; a.src_sel = 2; a.dst_sel = 3;
-        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
-        k_strided<T, -1><<<dim3(cdiv(d.Lx, a.TX), d.nz, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
-    }
+    launch_ypass<T, -1>(d, sys, nsys, pl, d.nz, d.ny, 1, d.Ly, 0, 2, 3, st);
     // 3. z: input at 1..nz, conj(G-hat), output extended 0..ez-1: w2 -> w1 [3][ez][Ly][Lx]
-    {
-        const int TX = strided_tx<T>(d.Lz, 3);
-        const size_t sm = 2 * (size_t)d.Lz * 3 * TX * sizeof(C);
-        k_fftz_green<T, true><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), NTH, sm, st>>>(d, pl.pz, twz, sys, TX, d.nz, 1, d.ez, 0, 3, 2);
-    }
+    launch_zpass<T, true>(d, sys, nsys, pl, d.nz, 1, d.ez, 0, 3, 2, st);
     // 4. inverse y FFT, keep 0..ey-1: w1 [3][ez][Ly][Lx] -> w2 [3][ez][ey][Lx]
-    {
-        StridedArgs a;
-        a.nlines = d.Lx; a.TX = strided_tx<T>(d.Ly, 1);
-        a.in_count = d.Ly; a.in_off = 0; a.out_count = d.ey; a.out_off = 0;
-        a.src_es = d.Lx; a.src_os1 = (long long)d.Ly * d.Lx; a.src_os2 = (long long)d.ez * d.Ly * d.Lx;
-        a.dst_es = d.Lx; a.dst_os1 = (long long)d.ey * d.Lx; a.dst_os2 = (long long)d.ez * d.ey * d.Lx;
-        a.ncomp = 3; a.src_sel = 2; a.dst_sel = 3;
-        const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
-        k_strided<T, 1><<<dim3(cdiv(d.Lx, a.TX), d.ez, 3 * nsys), NTH, sm, st>>>(pl.py, twy, a, sys);
-    }
+    launch_ypass<T, 1>(d, sys, nsys, pl, d.ez, d.Ly, 0, d.ey, 0, 2, 3, st);
     // 5. inverse x FFT, keep 0..ex-1: w2 [3][ez][ey][Lx] -> w1 [3][ez][ey][ex]
     {
         const int NL = generic_rows_nl<T>(d.Lx);
         const long long nrows = 3LL * d.ez * d.ey;
         const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+        smem_attr((const void*)k_rows<T, 1>, sm);
         k_rows<T, 1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, twx, sys, 3, 2, nrows, NL, d.Lx, 0, d.ex, 0);
     }
     // 6. transposed divergence + contraction -> w2 [6][N]
@@ -717,6 +1048,7 @@ cudaError_t fft3_inplace_setup(const Dims& d, const Plans& pl, double2* buf, int
         const int NL = generic_rows_nl<double>(d.Lx);
         const long long nrows = (long long)ncomp * d.Lz * d.Ly;
         const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
+        smem_attr((const void*)k_rows_raw<double, -1>, sm);
         k_rows_raw<double, -1><<<cdiv(nrows, NL), NTH, sm, st>>>(pl.px, (const C*)pl.twx, buf, buf, nrows, NL);
     }
     // y: lines along y, outer1 = z (Lz), comp
@@ -728,6 +1060,7 @@ cudaError_t fft3_inplace_setup(const Dims& d, const Plans& pl, double2* buf, int
         a.dst_es = a.src_es; a.dst_os1 = a.src_os1; a.dst_os2 = a.src_os2;
         a.ncomp = ncomp; a.src_sel = a.dst_sel = 0;
         const size_t sm = 2 * (size_t)d.Ly * a.TX * sizeof(C);
+        smem_attr((const void*)k_strided_raw<double, -1>, sm);
         k_strided_raw<double, -1><<<dim3(cdiv(d.Lx, a.TX), d.Lz, ncomp), NTH, sm, st>>>(pl.py, (const C*)pl.twy, a, buf, buf);
     }
     // z: lines along z, outer1 = y (Ly), comp
@@ -739,6 +1072,7 @@ cudaError_t fft3_inplace_setup(const Dims& d, const Plans& pl, double2* buf, int
         a.dst_es = a.src_es; a.dst_os1 = a.src_os1; a.dst_os2 = a.src_os2;
         a.ncomp = ncomp; a.src_sel = a.dst_sel = 0;
         const size_t sm = 2 * (size_t)d.Lz * a.TX * sizeof(C);
+        smem_attr((const void*)k_strided_raw<double, -1>, sm);
         k_strided_raw<double, -1><<<dim3(cdiv(d.Lx, a.TX), d.Ly, ncomp), NTH, sm, st>>>(pl.pz, (const C*)pl.twz, a, buf, buf);
     }
     if (nl) *nl += 3;
@@ -753,10 +1087,11 @@ cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* o
 }
 
 void ktimer_mark(KTimer* t, int stage, bool f32, cudaStream_t st, int end) {
-    if (!t || t->stage != stage || t->f32 != (int)f32 || !t->ev) return;
+    if (!t || !t->on || !t->ev) return;
     if (!end) {
         if (t->used >= t->cap) return;
         cudaEventRecord(t->ev[2 * t->used], st);
+        t->tag[t->used] = (f32 ? 6 : 0) + stage;
         t->open = 1;
     } else if (t->open) {
         cudaEventRecord(t->ev[2 * t->used + 1], st);
@@ -771,37 +1106,16 @@ void ktimer_flush(KTimer* t) {
     for (int i = 0; i < t->used; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t->ev[2 * i], t->ev[2 * i + 1]) == cudaSuccess) {
-            t->ms += ms;
-            t->launches++;
+            t->ms[t->tag[i]] += ms;
+            t->launches[t->tag[i]]++;
         }
     }
     t->used = 0;
 }
 
 cudaError_t init_kernel_attributes() {
-    const int cap = 200 * 1024;
-    cudaError_t e = cudaSuccess;
-#define LSM_ATTR(K) if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)
-    LSM_ATTR(k_div_fftx<float>);
-    LSM_ATTR(k_div_fftx<double>);
-    LSM_ATTR((k_strided<float, -1>));
-    LSM_ATTR((k_strided<float, 1>));
-    LSM_ATTR((k_strided<double, -1>));
-    LSM_ATTR((k_strided<double, 1>));
-    LSM_ATTR((k_strided_raw<double, -1>));
-    LSM_ATTR((k_fftz_green<float, false>));
-    LSM_ATTR((k_fftz_green<float, true>));
-    LSM_ATTR((k_fftz_green<double, false>));
-    LSM_ATTR((k_fftz_green<double, true>));
-    LSM_ATTR(k_fftx_out<float>);
-    LSM_ATTR(k_fftx_out<double>);
-    LSM_ATTR((k_rows<float, -1>));
-    LSM_ATTR((k_rows<float, 1>));
-    LSM_ATTR((k_rows<double, -1>));
-    LSM_ATTR((k_rows<double, 1>));
-    LSM_ATTR((k_rows_raw<double, -1>));
-#undef LSM_ATTR
-    return e;
+    // dynamic shared-memory limits are raised lazily per kernel (smem_attr)
+    return cudaSuccess;
 }
 
 }  // namespace lsm

@@ -43,6 +43,18 @@ template <typename C> __device__ __forceinline__ C from_d2(double2 a);
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 
+// Asynchronous global -> shared copies (sm_80+ cp.async): 8- or 16-byte elements.
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* smem_dst, const C* gmem_src) {
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem_dst);
+    if (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Grid geometry of one medium.  Model nodes n_a; padded periodic length L_a = 2 n_a;
 // extended contrast-source nodes e_a = n_a + 2 (nodes -1 .. n_a).
 struct Dims {

@@ -1,0 +1,177 @@
+// fft4.cuh - compile-time two-step ("four-step") FFT of lines held in shared memory.
+//
+// A line of length L = A * B is transformed as
+//   Y[t][k1] = W_L^(t k1) * sum_a x[t + B a] W_A^(a k1)      (B DFTs of length A, then twiddles)
+//   X[k1 + A k2] = sum_t Y[t][k1] W_B^(t k2)                  (A DFTs of length B)
+// with every short DFT held in registers.  Each of the two steps reads its inputs from shared
+// memory into registers, synchronises, and writes its outputs back in place, so one buffer of
+// L * LD elements suffices.  A tile of NL lines is transformed by exactly NL * min(A, B)
+// threads: thread tid works on line tid % NL.  Line l, element e sits at s[e * LD + l].
+#pragma once
+#include "fft.cuh"
+
+namespace lsm {
+
+template <int S, typename C>
+__device__ __forceinline__ C cmul_const(C a, double re, double im_s) {
+    // multiply by (re + S * i * im_s)
+    typedef typename real_of<C>::type T;
+    const T cr = (T)re, ci = (T)(S * im_s);
+    return mkc<C>(a.x * cr - a.y * ci, a.x * ci + a.y * cr);
+}
+
+// 16-point DFT in registers, natural order in and out: n = 4 n1 + n2, k = k1 + 4 k2.
+template <int S, typename C> __device__ __forceinline__ void bfly16(C* v) {
+    const double c1 = 0.92387953251128675613;  // cos(pi/8)
+    const double s1 = 0.38268343236508977173;  // sin(pi/8)
+    const double r2 = 0.70710678118654752440;  // 1/sqrt(2)
+    C y[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+        bfly4<S>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = a[k1];
+    }
+    // twiddles W16^(n2 k1), W16^m = cos(2 pi m/16) + S i sin(2 pi m/16)
+    y[5] = cmul_const<S>(y[5], c1, s1);      // m = 1
+    y[6] = cmul_const<S>(y[6], r2, r2);      // m = 2
+    y[7] = cmul_const<S>(y[7], s1, c1);      // m = 3
+    y[9] = cmul_const<S>(y[9], r2, r2);      // m = 2
+    y[10] = cmul_si<S>(y[10]);               // m = 4
+    y[11] = cmul_const<S>(y[11], -r2, r2);   // m = 6
+    y[13] = cmul_const<S>(y[13], s1, c1);    // m = 3
+    y[14] = cmul_const<S>(y[14], -r2, r2);   // m = 6
+    y[15] = cmul_const<S>(y[15], -c1, -s1);  // m = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C b[4] = {y[k1], y[4 + k1], y[8 + k1], y[12 + k1]};
+        bfly4<S>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+    }
+}
+
+template <int R, int S, typename C> __device__ __forceinline__ void dft_reg(C* v) {
+    if (R == 2) bfly2<S>(v);
+    else if (R == 4) bfly4<S>(v);
+    else if (R == 8) bfly8<S>(v);
+    else bfly16<S>(v);
+}
+
+template <int A, int B> struct FourStep {
+    static constexpr int L = A * B;
+    static constexpr int TPL = A < B ? A : B;   // threads per line
+    static constexpr int I1 = B / TPL;          // step-1 DFTs per thread
+    static constexpr int I2 = A / TPL;          // step-2 DFTs per thread
+};
+
+// In-place FFT (sign S) of NL lines; called by exactly NL * TPL threads, tid < NL * TPL.
+// The caller synchronises before (input written) and gets the result after the final barrier.
+template <int A, int B, int S, typename C>
+__device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restrict__ tw, int tid) {
+    typedef FourStep<A, B> F;
+    const int l = tid % NL;
+    const int q = tid / NL;
+    C v[F::I1][A];
+#pragma unroll
+    for (int i = 0; i < F::I1; ++i) {
+        const int t = q + F::TPL * i;
+#pragma unroll
+        for (int a = 0; a < A; ++a) v[i][a] = s[(t + B * a) * LD + l];
+        dft_reg<A, S>(v[i]);
+        if (t) {
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) {
+                C w = __ldg(&tw[t * k1]);
+                if (S > 0) w.y = -w.y;
+                v[i][k1] = cmul(v[i][k1], w);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < F::I1; ++i) {
+        const int t = q + F::TPL * i;
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) s[(t * A + k1) * LD + l] = v[i][k1];
+    }
+    __syncthreads();
+    C w2[F::I2][B];
+#pragma unroll
+    for (int i = 0; i < F::I2; ++i) {
+        const int k1 = q + F::TPL * i;
+#pragma unroll
+        for (int t = 0; t < B; ++t) w2[i][t] = s[(t * A + k1) * LD + l];
+        dft_reg<B, S>(w2[i]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < F::I2; ++i) {
+        const int k1 = q + F::TPL * i;
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) s[(k1 + A * k2) * LD + l] = w2[i][k2];
+    }
+    __syncthreads();
+}
+
+}  // namespace lsm
+
+namespace lsm {
+
+// Four-step FFT with caller-supplied input and output.  ld(l, e) returns element e of line l
+// (IN_SMEM: it reads the buffer s itself, so a barrier separates those reads from the first
+// write into s); st(l, k, v) receives output k of line l (OUT_SMEM: it writes s, so a barrier
+// separates the last reads of s from those writes).  Called by exactly NL * TPL threads.
+template <int A, int B, int S, bool IN_SMEM, bool OUT_SMEM, typename C, class Ld, class St>
+__device__ __forceinline__ void fft4_io(C* s, int NL, int LD, const C* __restrict__ tw, int tid, Ld ld, St st) {
+    typedef FourStep<A, B> F;
+    const int l = tid % NL;
+    const int q = tid / NL;
+    C v[F::I1][A];
+#pragma unroll
+    for (int i = 0; i < F::I1; ++i) {
+        const int t = q + F::TPL * i;
+#pragma unroll
+        for (int a = 0; a < A; ++a) v[i][a] = ld(l, t + B * a);
+    }
+#pragma unroll
+    for (int i = 0; i < F::I1; ++i) {
+        const int t = q + F::TPL * i;
+        dft_reg<A, S>(v[i]);
+        if (t) {
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) {
+                C w = __ldg(&tw[t * k1]);
+                if (S > 0) w.y = -w.y;
+                v[i][k1] = cmul(v[i][k1], w);
+            }
+        }
+    }
+    if (IN_SMEM) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < F::I1; ++i) {
+        const int t = q + F::TPL * i;
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) s[(t * A + k1) * LD + l] = v[i][k1];
+    }
+    __syncthreads();
+    C w2[F::I2][B];
+#pragma unroll
+    for (int i = 0; i < F::I2; ++i) {
+        const int k1 = q + F::TPL * i;
+#pragma unroll
+        for (int t = 0; t < B; ++t) w2[i][t] = s[(t * A + k1) * LD + l];
+        dft_reg<B, S>(w2[i]);
+    }
+    if (OUT_SMEM) __syncthreads();
+#pragma unroll
+    for (int i = 0; i < F::I2; ++i) {
+        const int k1 = q + F::TPL * i;
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) st(l, k1 + A * k2, w2[i][k2]);
+    }
+    if (OUT_SMEM) __syncthreads();
+}
+
+}  // namespace lsm

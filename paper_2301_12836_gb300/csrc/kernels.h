@@ -20,17 +20,17 @@ struct ApplySys {
     unsigned long long* count;  // incremented once per executed system apply (may be nullptr)
 };
 
-// CUDA-event timing of one stage of the apply (diagnostics).  Stages: 0 stress, 1 div+fftx,
-// 2 fft y forward, 3 fft z + Green multiply, 4 fft y inverse, 5 fftx inverse + epilogue.
+// CUDA-event timing of every stage of the apply, per precision (diagnostics).  Stages: 0 stress,
+// 1 div+fftx, 2 fft y forward, 3 fft z + Green multiply, 4 fft y inverse, 5 fftx inverse + epilogue.
 struct KTimer {
-    int stage = -1;
-    int f32 = 1;
+    int on = 0;
     cudaEvent_t* ev = nullptr;   // 2 * cap events
+    int* tag = nullptr;          // slot of each recorded pair: precision * 6 + stage (precision 1 = FP32)
     int cap = 0;
     int used = 0;
     int open = 0;
-    double ms = 0.0;             // flushed total
-    long long launches = 0;      // flushed launches
+    double ms[12] = {0};         // flushed totals per slot
+    long long launches[12] = {0};
 };
 void ktimer_mark(KTimer* t, int stage, bool f32, cudaStream_t st, int end);
 void ktimer_flush(KTimer* t);

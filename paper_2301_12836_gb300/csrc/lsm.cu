@@ -143,6 +143,7 @@ void store_release(Store* s) {
     if (s->timer.ev) {
         for (int i = 0; i < 2 * s->timer.cap; ++i) cudaEventDestroy(s->timer.ev[i]);
         delete[] s->timer.ev;
+        delete[] s->timer.tag;
     }
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
     cudaFree(s->ws.block);
@@ -717,40 +718,44 @@ extern "C" lsm_status lsm_solve(lsm_t h, const void* b, void* x, int* iters, dou
     return lsm_solve_batched(1, &h, bb, xx, iters, relres, nullptr);
 }
 
-extern "C" lsm_status lsm_timer_start(lsm_t h, int stage, int precision) {
+extern "C" lsm_status lsm_timer_start(lsm_t h, int enable) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_timer_start: null handle");
-    if (stage < -1 || stage > 5 || (precision != LSM_FP64 && precision != LSM_MIXED))
-        return fail(h, LSM_ERR_ARG, "lsm_timer_start: stage must be -1..5, precision LSM_FP64 or LSM_MIXED");
     Store* s = h->s;
     CK(h, cudaStreamSynchronize(s->st));
     KTimer& t = s->timer;
     if (!t.ev) {
         t.cap = 4096;
         t.ev = new cudaEvent_t[2 * t.cap];
+        t.tag = new int[t.cap];
         for (int i = 0; i < 2 * t.cap; ++i) CK(h, cudaEventCreate(&t.ev[i]));
     }
-    t.stage = stage;
-    t.f32 = precision == LSM_MIXED ? 1 : 0;
+    t.on = enable ? 1 : 0;
     t.used = 0;
     t.open = 0;
-    t.ms = 0.0;
-    t.launches = 0;
+    for (int i = 0; i < 12; ++i) {
+        t.ms[i] = 0.0;
+        t.launches[i] = 0;
+    }
     CK(h, cudaMemsetAsync(s->counts, 0, 2 * sizeof(unsigned long long), s->st));
     CK(h, cudaStreamSynchronize(s->st));
     return LSM_OK;
 }
 
-extern "C" lsm_status lsm_timer_read(lsm_t h, double* ms, long long* launches, long long* applies64, long long* applies32) {
+extern "C" lsm_status lsm_timer_read(lsm_t h, double ms[12], long long launches[12], long long applies[2]) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_timer_read: null handle");
     Store* s = h->s;
     CK(h, cudaStreamSynchronize(s->st));
     ktimer_flush(&s->timer);
     unsigned long long c[2] = {0, 0};
     CK(h, cudaMemcpy(c, s->counts, sizeof(c), cudaMemcpyDeviceToHost));
-    if (ms) *ms = s->timer.ms;
-    if (launches) *launches = s->timer.launches;
-    if (applies64) *applies64 = (long long)c[0];
-    if (applies32) *applies32 = (long long)c[1];
+    for (int i = 0; i < 12; ++i) {
+        if (ms) ms[i] = s->timer.ms[i];
+        if (launches) launches[i] = s->timer.launches[i];
+    }
+    if (applies) {
+        applies[0] = (long long)c[0];
+        applies[1] = (long long)c[1];
+    }
     return LSM_OK;
 }
 

@@ -78,10 +78,9 @@ def load(path: str = LIB_PATH):
     lib.lsm_solve_batched.restype = i
     lib.lsm_launch_count.argtypes = [vp]
     lib.lsm_launch_count.restype = ct.c_longlong
-    lib.lsm_timer_start.argtypes = [vp, i, i]
+    lib.lsm_timer_start.argtypes = [vp, i]
     lib.lsm_timer_start.restype = i
-    lib.lsm_timer_read.argtypes = [vp, ct.POINTER(d), ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong),
-                                   ct.POINTER(ct.c_longlong)]
+    lib.lsm_timer_read.argtypes = [vp, ct.POINTER(d), ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]
     lib.lsm_timer_read.restype = i
     lib.lsm_apply_static.argtypes = [vp, vp, vp]
     lib.lsm_apply_static.restype = i
@@ -211,16 +210,17 @@ def lsm_launch_count(h: Handle) -> int:
     return int(load().lsm_launch_count(h.ptr))
 
 
-def lsm_timer_start(h: Handle, stage: int, precision: int) -> None:
-    _check(load().lsm_timer_start(h.ptr, int(stage), int(precision)), h.ptr)
+def lsm_timer_start(h: Handle, enable: bool = True) -> None:
+    _check(load().lsm_timer_start(h.ptr, 1 if enable else 0), h.ptr)
 
 
 def lsm_timer_read(h: Handle):
-    """Returns (milliseconds, launches, FP64 system applies, FP32 system applies) since lsm_timer_start."""
-    ms = ct.c_double(0.0)
-    nl, a64, a32 = ct.c_longlong(0), ct.c_longlong(0), ct.c_longlong(0)
-    _check(load().lsm_timer_read(h.ptr, ct.byref(ms), ct.byref(nl), ct.byref(a64), ct.byref(a32)), h.ptr)
-    return ms.value, nl.value, a64.value, a32.value
+    """Returns (ms[12], launches[12], applies[2]) since lsm_timer_start; slot = 6 * p + stage, p = 1 for FP32."""
+    ms = (ct.c_double * 12)()
+    nl = (ct.c_longlong * 12)()
+    ap = (ct.c_longlong * 2)()
+    _check(load().lsm_timer_read(h.ptr, ms, nl, ap), h.ptr)
+    return list(ms), list(nl), list(ap)
 
 
 def lsm_apply_static(h: Handle, u: torch.Tensor, Au: torch.Tensor) -> None:
