@@ -376,10 +376,10 @@ def main():
         rec = {"kernel": name, "ms": round(st_ms[slot], 3), "launches": st_launch[slot],
                "share_of_step": round(st_ms[slot] / ms, 4)}
         if f32:
-            b = stage_bytes(stage, med.n, 8, 4)
-            ach = b * napp / (st_ms[slot] / 1e3) / 1e9
+            nbytes = stage_bytes(stage, med.n, 8, 4)
+            ach = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
             rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": b})
+                        "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": nbytes})
         else:
             fl = stage_flops(stage, med.n)
             ach = fl * napp / (st_ms[slot] / 1e3) / 1e12

@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(NTH) k_strided_raw(FftPlan p, const typename c
 }
 
 // four-step strided pass: step 1 loads straight from global memory, the last step stores straight
-// to global memory; one shared-memory exchange in between.  Block = TX * TPL threads.
-template <typename T, int DIR, int A, int B>
+// to global memory; one shared-memory exchange in between.  Block = TX * TPL threads, line l = lx.
+template <typename T, int DIR, int A, int B, int TX>
 __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const typename cplx_of<T>::type* __restrict__ tw,
                                                                      StridedArgs a, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
@@ -231,19 +231,21 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const ty
     const ApplySys<T> S = sys[sidx];
     if (S.run && !*S.run) return;
     C* s = reinterpret_cast<C*>(smem_raw);
-    const C* __restrict__ src = pick<C>(S, a.src_sel) + c * a.src_os2 + blockIdx.y * a.src_os1;
-    C* __restrict__ dst = pick<C>(S, a.dst_sel) + c * a.dst_os2 + blockIdx.y * a.dst_os1;
-    const int x0 = blockIdx.x * a.TX;
-    const int TX = a.TX;
-    auto ld = [&](int l, int e) -> C {
-        const int x = x0 + l, es = e - a.in_off;
-        return (x < a.nlines && es >= 0 && es < a.in_count) ? src[es * a.src_es + x] : czero<C>();
+    const int x = blockIdx.x * TX + threadIdx.x % TX;   // this thread's line
+    const bool xin = x < a.nlines;
+    const C* __restrict__ src = pick<C>(S, a.src_sel) + c * a.src_os2 + blockIdx.y * a.src_os1 + x;
+    C* __restrict__ dst = pick<C>(S, a.dst_sel) + c * a.dst_os2 + blockIdx.y * a.dst_os1 + x;
+    const int ses = (int)a.src_es, des = (int)a.dst_es;
+    const int in_off = a.in_off, in_count = a.in_count, out_off = a.out_off, out_count = a.out_count;
+    auto ld = [&](int, int e) -> C {
+        const int es = e - in_off;
+        return (xin && es >= 0 && es < in_count) ? src[es * ses] : czero<C>();
     };
-    auto st = [&](int l, int k, C v) {
-        const int x = x0 + l, eo = k - a.out_off;
-        if (x < a.nlines && eo >= 0 && eo < a.out_count) dst[eo * a.dst_es + x] = v;
+    auto st = [&](int, int k, C v) {
+        const int eo = k - out_off;
+        if (xin && eo >= 0 && eo < out_count) dst[eo * des] = v;
     };
-    fft4_io<A, B, DIR, false, false>(s, TX, TX, tw, threadIdx.x, ld, st);
+    fft4_io<A, B, DIR, false, false, TX>(s, tw, threadIdx.x, ld, st);
 }
 
 // four-step z pass with the Green multiply.  Block = 3 TX * TPL threads; line l = c * TX + lx.
@@ -251,26 +253,33 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const ty
 // the octant spectrum (|kz| = 0..nz, 6 components, TX values of kx at one ky) is copied to shared
 // memory asynchronously, once for all consecutive systems that share the spectrum (the sources
 // of one frequency), while the first of them runs its forward FFT.
-template <typename T, bool CONJ, int A, int B>
-__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftz_green(Dims d, const typename cplx_of<T>::type* __restrict__ tw,
-                                                                        const ApplySys<T>* __restrict__ sys, int nsys, int TX,
-                                                                        int in_count, int in_off, int out_count, int out_off,
-                                                                        int src_sel, int dst_sel) {
+template <typename T, bool CONJ, int A, int B, int TX>
+__global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 4 ? 3 : 1) k4_fftz_green(
+    Dims d, const typename cplx_of<T>::type* __restrict__ tw, const ApplySys<T>* __restrict__ sys, int nsys, int in_count,
+    int in_off, int out_count, int out_off, int src_sel, int dst_sel) {
     typedef typename cplx_of<T>::type C;
     typedef typename real_of<C>::type R;
+    constexpr int NL = 3 * TX;
+    constexpr int L = A * B;
+    constexpr int E = (int)(128 / sizeof(C));
+    // spectrum slice [nz+1][6][TX] with row stride GS: consecutive kz rows start TX elements
+    // apart modulo a 128-byte bank row, so the multiply's reads are conflict-free
+    constexpr int GS = 6 * TX + (((TX - 6 * TX) % E) + E) % E;
+    constexpr int YB = B * fft4_ystride<A, C>(NL);
     extern __shared__ unsigned char smem_raw[];
-    const int NL = 3 * TX;
-    const int L = d.Lz;
     C* s = reinterpret_cast<C*>(smem_raw);
-    C* sG = s + (size_t)L * NL;   // [nz + 1][6][TX]
+    C* sG = s + (YB > L * NL ? YB : L * NL);
     const int ky = blockIdx.y;
     const int x0 = blockIdx.x * TX;
     const int fy = ky <= d.ny ? ky : d.Ly - ky;
     const R sy = ky > d.ny ? (R)-1 : (R)1;
     const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
-    const long long plane = (long long)d.Ly * d.Lx;
-    const long long s_c = (long long)in_count * plane, d_c = (long long)out_count * plane;
-    const long long off = (long long)ky * d.Lx + x0;
+    const int plane = d.Ly * d.Lx;
+    // this thread's line (fixed through both FFTs): component cl, column x0 + lxl
+    const int lt = threadIdx.x % NL;
+    const int cl = lt / TX, lxl = lt - cl * TX;
+    const bool xin = x0 + lxl < d.Lx;
+    const long long col = (long long)ky * d.Lx + x0 + lxl;
     const C* staged = nullptr;
     for (int si = 0; si < nsys; ++si) {
         const ApplySys<T> S = sys[si];
@@ -287,20 +296,21 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftz_green(Dims 
                 const int kx = x0 + lx;
                 if (kx < d.Lx) {
                     const int fx = kx <= d.nx ? kx : d.Lx - kx;
-                    cp_async_elem(&sG[i], S.ghat + c * NO + ((long long)fz * (d.ny + 1) + fy) * (d.nx + 1) + fx);
+                    cp_async_elem(&sG[fz * GS + c * TX + lx],
+                                  S.ghat + c * NO + ((long long)fz * (d.ny + 1) + fy) * (d.nx + 1) + fx);
                 }
             }
             cp_async_commit();
             staged = S.ghat;
         }
-        const C* __restrict__ src = pick<C>(S, src_sel);
-        C* __restrict__ dst = pick<C>(S, dst_sel);
-        auto ld_g = [&](int l, int e) -> C {
-            const int c = l / TX, lx = l - c * TX, es = e - in_off;
-            return (x0 + lx < d.Lx && es >= 0 && es < in_count) ? src[c * s_c + es * plane + off + lx] : czero<C>();
+        const C* __restrict__ src = pick<C>(S, src_sel) + (long long)cl * in_count * plane + col;
+        C* __restrict__ dst = pick<C>(S, dst_sel) + (long long)cl * out_count * plane + col;
+        auto ld_g = [&](int, int e) -> C {
+            const int es = e - in_off;
+            return (xin && es >= 0 && es < in_count) ? src[es * plane] : czero<C>();
         };
         auto st_s = [&](int l, int k, C v) { s[k * NL + l] = v; };
-        fft4_io<A, B, -1, false, true>(s, NL, NL, tw, threadIdx.x, ld_g, st_s);
+        fft4_io<A, B, -1, false, true, NL>(s, tw, threadIdx.x, ld_g, st_s);
         if (fresh) {
             cp_async_wait_all();
             __syncthreads();
@@ -313,7 +323,7 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftz_green(Dims 
             const int fz = kz <= d.nz ? kz : L - kz;
             const R sz = kz > d.nz ? (R)-1 : (R)1;
             const R sx = kx > d.nx ? (R)-1 : (R)1;
-            const C* g = sG + fz * 6 * TX + lx;
+            const C* g = sG + fz * GS + lx;
             C G[6];
             G[0] = g[0];
             G[1] = g[TX];
@@ -333,11 +343,11 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftz_green(Dims 
         }
         __syncthreads();
         auto ld_s = [&](int l, int e) -> C { return s[e * NL + l]; };
-        auto st_g = [&](int l, int k, C v) {
-            const int c = l / TX, lx = l - c * TX, eo = k - out_off;
-            if (x0 + lx < d.Lx && eo >= 0 && eo < out_count) dst[c * d_c + eo * plane + off + lx] = v;
+        auto st_g = [&](int, int k, C v) {
+            const int eo = k - out_off;
+            if (xin && eo >= 0 && eo < out_count) dst[eo * plane] = v;
         };
-        fft4_io<A, B, 1, true, false>(s, NL, NL, tw, threadIdx.x, ld_s, st_g);
+        fft4_io<A, B, 1, true, false, NL>(s, tw, threadIdx.x, ld_s, st_g);
         __syncthreads();  // the next system's forward step writes s
     }
 }
@@ -840,9 +850,10 @@ template <typename T, class F>
 static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm) {
     typedef typename cplx_of<T>::type C;
     if constexpr (F::INPLACE) {
-        TX = sizeof(T) == 4 ? (ncomp == 1 ? 16 : 8) : (ncomp == 1 ? 8 : 4);
+        TX = sizeof(T) == 4 ? (ncomp == 1 ? 16 : 4) : (ncomp == 1 ? 8 : 4);
         threads = ncomp * TX * F::TPL;
-        sm = (size_t)L * ncomp * TX * sizeof(C);
+        const size_t ybuf = (size_t)F::B_ * fft4_ystride<F::A_, C>(ncomp * TX);
+        sm = (ybuf > (size_t)L * ncomp * TX ? ybuf : (size_t)L * ncomp * TX) * sizeof(C);
     } else {
         TX = strided_tx<T>(L, ncomp);
         threads = NTH;
@@ -911,9 +922,9 @@ static void launch_ypass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
         a.dst_es = d.Lx; a.dst_os1 = (long long)out_count * d.Lx; a.dst_os2 = (long long)planes * out_count * d.Lx;
         a.ncomp = 3; a.src_sel = src_sel; a.dst_sel = dst_sel;
         if constexpr (F::INPLACE) {
-            constexpr int A = F::A_, B = F::B_;
-            smem_attr((const void*)k4_strided<T, DIR, A, B>, sm);
-            k4_strided<T, DIR, A, B><<<dim3(cdiv(d.Lx, a.TX), planes, 3 * nsys), th, sm, st>>>((const C*)pl.twy, a, sys);
+            constexpr int A = F::A_, B = F::B_, TXC = sizeof(T) == 4 ? 16 : 8;
+            smem_attr((const void*)k4_strided<T, DIR, A, B, TXC>, sm);
+            k4_strided<T, DIR, A, B, TXC><<<dim3(cdiv(d.Lx, a.TX), planes, 3 * nsys), th, sm, st>>>((const C*)pl.twy, a, sys);
         } else {
             smem_attr((const void*)k_strided<T, DIR, F>, sm);
             k_strided<T, DIR, F><<<dim3(cdiv(d.Lx, a.TX), planes, 3 * nsys), th, sm, st>>>(pl.py, (const C*)pl.twy, a, sys);
@@ -930,12 +941,16 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
         int TX, th;
         size_t sm;
         strided_cfg<T, F>(d.Lz, 3, TX, th, sm);
-        if constexpr (F::INPLACE) sm += (size_t)(d.nz + 1) * 6 * TX * sizeof(C);  // spectrum slice
         if constexpr (F::INPLACE) {
-            constexpr int A = F::A_, B = F::B_;
-            smem_attr((const void*)k4_fftz_green<T, CONJ, A, B>, sm);
-            k4_fftz_green<T, CONJ, A, B><<<dim3(cdiv(d.Lx, TX), d.Ly, 1), th, sm, st>>>(
-                d, (const C*)pl.twz, sys, nsys, TX, in_count, in_off, out_count, out_off, src_sel, dst_sel);
+            const int E = (int)(128 / sizeof(C));
+            const int GS = 6 * TX + (((TX - 6 * TX) % E) + E) % E;
+            sm += (size_t)(d.nz + 1) * GS * sizeof(C);  // spectrum slice
+        }
+        if constexpr (F::INPLACE) {
+            constexpr int A = F::A_, B = F::B_, TXC = 4;
+            smem_attr((const void*)k4_fftz_green<T, CONJ, A, B, TXC>, sm);
+            k4_fftz_green<T, CONJ, A, B, TXC><<<dim3(cdiv(d.Lx, TXC), d.Ly, 1), th, sm, st>>>(
+                d, (const C*)pl.twz, sys, nsys, in_count, in_off, out_count, out_off, src_sel, dst_sel);
         } else {
             smem_attr((const void*)k_fftz_green<T, CONJ, F>, sm);
             k_fftz_green<T, CONJ, F><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), th, sm, st>>>(

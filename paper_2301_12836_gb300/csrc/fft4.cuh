@@ -119,15 +119,30 @@ __device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restr
 
 namespace lsm {
 
+// Row stride (in elements) of the step-1 intermediate Y[t][k1] of fft4_io.  Threads of a warp
+// write Y for consecutive t (groups of NL lanes) and read it back for consecutive k1; the skew
+// PAD makes each group start on the banks where the previous one ended, so both accesses cost
+// the minimum number of shared-memory wavefronts.  E = elements per 128-byte bank row.
+template <int A, int E>
+__host__ __device__ constexpr int fft4_pad(int NL) {
+    return ((NL - A * NL) % E + E) % E;
+}
+template <int A, typename C>
+__host__ __device__ constexpr int fft4_ystride(int NL) {
+    return A * NL + fft4_pad<A, (int)(128 / sizeof(C))>(NL);
+}
+
 // Four-step FFT with caller-supplied input and output.  ld(l, e) returns element e of line l
 // (IN_SMEM: it reads the buffer s itself, so a barrier separates those reads from the first
 // write into s); st(l, k, v) receives output k of line l (OUT_SMEM: it writes s, so a barrier
-// separates the last reads of s from those writes).  Called by exactly NL * TPL threads.
-template <int A, int B, int S, bool IN_SMEM, bool OUT_SMEM, typename C, class Ld, class St>
-__device__ __forceinline__ void fft4_io(C* s, int NL, int LD, const C* __restrict__ tw, int tid, Ld ld, St st) {
+// separates the last reads of s from those writes).  Called by exactly NL * TPL threads.  The
+// intermediate occupies B * fft4_ystride<A, C>(NL) elements of s.
+template <int A, int B, int S, bool IN_SMEM, bool OUT_SMEM, int NL, typename C, class Ld, class St>
+__device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid, Ld ld, St st) {
     typedef FourStep<A, B> F;
     const int l = tid % NL;
     const int q = tid / NL;
+    constexpr int YS = fft4_ystride<A, C>(NL);
     C v[F::I1][A];
 #pragma unroll
     for (int i = 0; i < F::I1; ++i) {
@@ -153,7 +168,7 @@ __device__ __forceinline__ void fft4_io(C* s, int NL, int LD, const C* __restric
     for (int i = 0; i < F::I1; ++i) {
         const int t = q + F::TPL * i;
 #pragma unroll
-        for (int k1 = 0; k1 < A; ++k1) s[(t * A + k1) * LD + l] = v[i][k1];
+        for (int k1 = 0; k1 < A; ++k1) s[t * YS + k1 * NL + l] = v[i][k1];
     }
     __syncthreads();
     C w2[F::I2][B];
@@ -161,7 +176,7 @@ __device__ __forceinline__ void fft4_io(C* s, int NL, int LD, const C* __restric
     for (int i = 0; i < F::I2; ++i) {
         const int k1 = q + F::TPL * i;
 #pragma unroll
-        for (int t = 0; t < B; ++t) w2[i][t] = s[(t * A + k1) * LD + l];
+        for (int t = 0; t < B; ++t) w2[i][t] = s[t * YS + k1 * NL + l];
         dft_reg<B, S>(w2[i]);
     }
     if (OUT_SMEM) __syncthreads();
