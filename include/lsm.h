@@ -170,6 +170,39 @@ lsm_status lsm_solve(lsm_t h, const void *b, void *x, int *iters, double *relres
 lsm_status lsm_solve_batched(int nsys, const lsm_t *hs, const void *const *b, void *const *x,
                              int *iters, double *relres, lsm_status *status);
 
+/*
+ * Adjoint solve A^H x = b (BiCGSTAB with the adjoint apply, same options and stopping rule as
+ * lsm_solve).  With b = R^T g (receiver-sampling adjoint of a misfit gradient g) the solution is
+ * the adjoint field lambda of the discrete-adjoint gradient of the LS solution (Sec. 3.2, Eq. 21).
+ *   b, x, iters, relres  as in lsm_solve (relres is ||b - A^H x|| / ||b||).
+ */
+lsm_status lsm_solve_adjoint(lsm_t h, const void *b, void *x, int *iters, double *relres);
+
+/*
+ * Replace the medium's contrast (all handles sharing it see the change; the Green spectra do not
+ * depend on the contrast and are kept).  dC, drho: device float64, layouts as in lsm_create; copied.
+ */
+lsm_status lsm_set_contrast(lsm_t h, const double *dC, const double *drho);
+
+/*
+ * Contrast gradient of the LS solution (discrete adjoint of Eqs. 8, 11 and 18): for the forward
+ * solution u (A u = u0) and an adjoint field lam (A^H lam = r), writes the gradient of
+ * Re<lam, K (Dv dC eps(u) + w^2 drho u)> = Re<r, du> with respect to
+ *   gC    device float64 [21][nz][ny][nx]: the 21 packed Voigt contrast planes (an off-diagonal
+ *         entry counts both of its symmetric positions),
+ *   grho  device float64 [nz][ny][nx]: the density contrast;
+ * accumulate != 0 adds to gC and grho (sums over frequencies and sources), else overwrites.
+ * u, lam: device complex128, 3 * nz*ny*nx.
+ */
+lsm_status lsm_gradient(lsm_t h, const void *u, const void *lam, double *gC, double *grho, int accumulate);
+
+/*
+ * Moment-tensor gradient gM_J = Re<lam, d u0/d M_J> (Eqs. 13-16; u0 is linear in M), J over the
+ * Voigt components (M11, M22, M33, M23, M13, M12), for a source at xs [m].
+ *   lam  device complex128, 3 * nz*ny*nx;  gM  host double[6] (written).  Synchronises the stream.
+ */
+lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const void *lam, double gM[6]);
+
 /* Number of kernel launches the library has issued on this handle (diagnostics). */
 long long lsm_launch_count(lsm_t h);
 

@@ -367,3 +367,48 @@ def apply_at_points(u, medium, omega, points, mode="exact"):
         us = np.einsum("zyxij,jzyx->i", T, q)
         out.append(u[:, iz, iy, ix] - us)
     return np.array(out)
+
+
+def kernel_adjoint_ext(lam, medium, omega, mode="exact"):
+    """z = K_T^H lam on the extended nodes [-1, n]^3: z(p) = sum_x conj(T(x - p)) lam(x).
+
+    By FFT on the 2n-periodic grid: lam placed at its nodes, multiplied by conj(T-hat)
+    (T is even and symmetric), read back at the extended nodes p mod 2n.
+    Returns (3, nz+2, ny+2, nx+2); index p holds node p - 1.
+    """
+    nx, ny, nz = medium.n
+    T = _green.kernel_table(medium.n, medium.h, omega, medium.lam0, medium.mu0, medium.rho0, mode)
+    That = np.fft.fftn(T, axes=(-3, -2, -1))
+    P = (2 * nz, 2 * ny, 2 * nx)
+    Lp = np.zeros((3,) + P, dtype=np.complex128)
+    Lp[:, :nz, :ny, :nx] = lam
+    zh = np.einsum("ij...,i...->j...", np.conj(That), np.fft.fftn(Lp, axes=(-3, -2, -1)))
+    zper = np.fft.ifftn(zh, axes=(-3, -2, -1))
+    iz = np.arange(-1, nz + 1) % (2 * nz)
+    iy = np.arange(-1, ny + 1) % (2 * ny)
+    ix = np.arange(-1, nx + 1) % (2 * nx)
+    return zper[:, iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+
+
+def contrast_gradient(u, lam, medium, omega, mode="exact"):
+    """Gradients of Re<lam, K_T (Dv dC eps(u) + w^2 Emb drho u)> with respect to the 21 packed
+    contrast planes and the density contrast (the discrete adjoint of Eqs. 8 and 11).
+
+    tau = Dv^T z (Voigt, model nodes) with z = K_T^H lam; for packed entry (I, J):
+    Re(conj(tau_I) eps_J) (+ Re(conj(tau_J) eps_I) when I != J); density: w^2 Re(sum_j conj(z_j) u_j).
+    Returns (gC (21, nz, ny, nx), grho (nz, ny, nx)).
+    """
+    nx, ny, nz = medium.n
+    z = kernel_adjoint_ext(lam, medium, omega, mode)
+    Dv = divergence_matrix(medium.n, medium.h)
+    tau = (Dv.T @ z.reshape(-1)).reshape(6, nz, ny, nx)
+    eps = strain(u, medium.h)
+    gC = np.zeros((21, nz, ny, nx))
+    for k, (I, J) in enumerate(_TRIU):
+        g = np.real(np.conj(tau[I]) * eps[J])
+        if I != J:
+            g = g + np.real(np.conj(tau[J]) * eps[I])
+        gC[k] = g
+    zin = z[:, 1:-1, 1:-1, 1:-1]
+    grho = omega ** 2 * np.real(np.sum(np.conj(zin) * u, axis=0))
+    return gC, grho

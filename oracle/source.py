@@ -47,3 +47,14 @@ def point_force_field(n, h, table, node, comp):
     my = (Y - node[1]) % (2 * ny)
     mx = (X - node[0]) % (2 * nx)
     return np.stack([table[i, comp][mz, my, mx] for i in range(3)])
+
+
+def moment_gradient(lam, n, h, xs, omega, lam0, mu0, rho0, mode="exact"):
+    """Re<lam, d u0 / d M_J> for the six Voigt components (u0 is linear in M, Eqs. 13-16)."""
+    out = np.zeros(6)
+    for J in range(6):
+        e = np.zeros(6)
+        e[J] = 1.0
+        u0, _ = background_field(n, h, e, xs, omega, lam0, mu0, rho0, mode)
+        out[J] = np.real(np.vdot(lam, u0))
+    return out

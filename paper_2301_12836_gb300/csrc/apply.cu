@@ -996,13 +996,11 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
     return cudaGetLastError();
 }
 
+// z = K_T^H u on the extended nodes, left in w1 [3][ez][ey][ex] (the first five steps of A^H).
 template <typename T>
-cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
-                           long long* nl) {
+static void launch_adjoint_conv(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st) {
     typedef typename cplx_of<T>::type C;
     const Dims& d = m.d;
-    const T* dC = (const T*)m.dC;
-    const T* drho = (const T*)m.drho;
     const C* twx = (const C*)pl.twx;
     // 1. w placed at x positions 1..nx, forward x FFT: u [3][nz][ny][nx] -> w1 [3][nz][ny][Lx]
     {
@@ -1026,11 +1024,93 @@ cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* 
         smem_attr((const void*)k_rows<T, 1>, sm);
         k_rows<T, 1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, twx, sys, 3, 2, nrows, NL, d.Lx, 0, d.ex, 0);
     }
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
+                           long long* nl) {
+    const Dims& d = m.d;
+    const T* dC = (const T*)m.dC;
+    const T* drho = (const T*)m.drho;
+    launch_adjoint_conv<T>(m, pl, sys, nsys, st);
     // 6. transposed divergence + contraction -> w2 [6][N]
     k_adj_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
     // 7. transposed strain + density, AH w = w - (...)
     k_adj_out<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, drho, sys);
     if (nl) *nl += 7;
+    return cudaGetLastError();
+}
+
+// Gradient of Re<lam, K_T (Dv dC eps(u) + w^2 Emb drho u)> (discrete adjoint of Eqs. 8, 11):
+// z = K_T^H lam (extended nodes, in w1), tau = Dv^T z; packed entry (I, J) gets
+// Re(conj(tau_I) eps_J) (+ Re(conj(tau_J) eps_I) for I != J), drho gets w^2 Re(sum_j conj(z_j) u_j).
+__global__ void __launch_bounds__(NTH) k_grad(Dims d, const ApplySys<double>* __restrict__ sys, const double2* __restrict__ u,
+                                              double* __restrict__ gC, double* __restrict__ grho, int accumulate) {
+    typedef double2 C;
+    const ApplySys<double> S = sys[0];
+    const C* __restrict__ z = S.w1;
+    const long long N = d.N;
+    const long long E = (long long)d.ex * d.ey * d.ez;
+    const double ih = 1.0 / d.h, i2h = 0.5 / d.h;
+    const long long sxy = (long long)d.nx * d.ny;
+    for (long long idx = (long long)blockIdx.x * NTH + threadIdx.x; idx < N; idx += (long long)gridDim.x * NTH) {
+        const int ix = (int)(idx % d.nx);
+        const int iy = (int)((idx / d.nx) % d.ny);
+        const int iz = (int)(idx / sxy);
+        auto der = [&](int c, int a) -> C {
+            const C* f = u + c * N;
+            const int i = a == 0 ? ix : (a == 1 ? iy : iz);
+            const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
+            const long long s = a == 0 ? 1 : (a == 1 ? (long long)d.nx : sxy);
+            if (i == 0) return cscale(csub(f[idx + s], f[idx]), ih);
+            if (i == n - 1) return cscale(csub(f[idx], f[idx - s]), ih);
+            return cscale(csub(f[idx + s], f[idx - s]), i2h);
+        };
+        C e[6];
+        e[0] = der(0, 0);
+        e[1] = der(1, 1);
+        e[2] = der(2, 2);
+        e[3] = cadd(der(1, 2), der(2, 1));
+        e[4] = cadd(der(0, 2), der(2, 0));
+        e[5] = cadd(der(0, 1), der(1, 0));
+        const long long e0 = ((long long)(iz + 1) * d.ey + (iy + 1)) * d.ex + (ix + 1);
+        const long long st[3] = {1, (long long)d.ex, (long long)d.ex * d.ey};
+        C tau[6];
+#pragma unroll
+        for (int J = 0; J < 6; ++J) tau[J] = czero<C>();
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const C* zj = z + j * E;
+                tau[t2v(j, k)] = cadd(tau[t2v(j, k)], cscale(csub(zj[e0 - st[k]], zj[e0 + st[k]]), i2h));
+            }
+        int k = 0;
+#pragma unroll
+        for (int I = 0; I < 6; ++I)
+#pragma unroll
+            for (int J = I; J < 6; ++J, ++k) {
+                double g = tau[I].x * e[J].x + tau[I].y * e[J].y;
+                if (I != J) g += tau[J].x * e[I].x + tau[J].y * e[I].y;
+                double* dst = gC + (long long)k * N + idx;
+                *dst = accumulate ? *dst + g : g;
+            }
+        double r = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const C zj = z[j * E + e0], uj = u[j * N + idx];
+            r += zj.x * uj.x + zj.y * uj.y;
+        }
+        r *= S.omega2;
+        grho[idx] = accumulate ? grho[idx] + r : r;
+    }
+}
+
+cudaError_t launch_gradient(const Medium& m, const Plans& pl, const ApplySys<double>* sys, const double2* u, double* gC,
+                            double* grho, int accumulate, cudaStream_t st, long long* nl) {
+    launch_adjoint_conv<double>(m, pl, sys, 1, st);
+    k_grad<<<grid_elems(m.d.N), NTH, 0, st>>>(m.d, sys, u, gC, grho, accumulate);
+    if (nl) *nl += 6;
     return cudaGetLastError();
 }
 

@@ -147,6 +147,67 @@ __global__ void k_source(Dims d, GreenPar p, double M11, double M22, double M33,
     }
 }
 
+// Re<lam, d u0/d M_J> for the unit Voigt moments e_J (M23 = M32 = 1 for J = 3, and so on):
+// u0_i(e_J) = -[(f' + g/r) (E_J g)_i + (g' - 2 g/r)(g.E_J g) g_i + (g/r) tr(E_J) g_i].
+// Block b writes its six partial sums to partial[b * 6 + J]; k_sum6 adds them in block order.
+constexpr int SG_BLOCKS = 4096;
+__global__ void __launch_bounds__(256) k_source_grad(Dims d, GreenPar p, double sx, double sy, double sz,
+                                                     const double2* __restrict__ lamv, double* __restrict__ partial) {
+    const long long N = d.N;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % d.nx);
+        const int iy = (int)((i / d.nx) % d.ny);
+        const int iz = (int)(i / ((long long)d.nx * d.ny));
+        const double x = ix * d.h - sx, y = iy * d.h - sy, z = iz * d.h - sz;
+        const double r = sqrt(x * x + y * y + z * z);
+        if (r == 0.0) continue;  // u0 is zero on a node that coincides with the source
+        const double g[3] = {x / r, y / r, z / r};
+        double2 f, gg, fp, gp;
+        radial(p, r, f, gg, fp, gp);
+        const double ir = 1.0 / r;
+        const double2 A = make_double2(fp.x + gg.x * ir, fp.y + gg.y * ir);
+        const double2 B = make_double2(gp.x - 2.0 * gg.x * ir, gp.y - 2.0 * gg.y * ir);
+        const double2 Cc = make_double2(gg.x * ir, gg.y * ir);
+        double2 l[3];
+        for (int c = 0; c < 3; ++c) l[c] = lamv[c * N + i];
+        // Voigt pairs of e_J: 11, 22, 33, 23, 13, 12
+        const int pa[6] = {0, 1, 2, 1, 0, 0}, pb[6] = {0, 1, 2, 2, 2, 1};
+        for (int J = 0; J < 6; ++J) {
+            double Mg[3] = {0, 0, 0};
+            Mg[pa[J]] += g[pb[J]];
+            if (pa[J] != pb[J]) Mg[pb[J]] += g[pa[J]];
+            const double gMg = g[0] * Mg[0] + g[1] * Mg[1] + g[2] * Mg[2];
+            const double tr = J < 3 ? 1.0 : 0.0;
+            double s = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double s1 = Mg[c], s2 = gMg * g[c], s3 = tr * g[c];
+                const double ux = -(A.x * s1 + B.x * s2 + Cc.x * s3), uy = -(A.y * s1 + B.y * s2 + Cc.y * s3);
+                s += l[c].x * ux + l[c].y * uy;   // Re(conj(lam) u0)
+            }
+            acc[J] += s;
+        }
+    }
+    __shared__ double sh[6][256];
+    for (int J = 0; J < 6; ++J) sh[J][threadIdx.x] = acc[J];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int J = 0; J < 6; ++J) sh[J][threadIdx.x] += sh[J][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int J = 0; J < 6; ++J) partial[blockIdx.x * 6 + J] = sh[J][0];
+}
+
+__global__ void k_sum6(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partial[b * 6 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
 static inline int gsz(long long n) {
     long long b = (n + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
@@ -193,6 +254,24 @@ cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, doub
     p.mode = green;
     k_source<<<gsz(d.N), 256, 0, st>>>(d, p, M6[0], M6[1], M6[2], M6[3], M6[4], M6[5], xs[0], xs[1], xs[2], u0, flag);
     if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_gradient(const Dims& d, double lam, double mu, double rho, double omega, int green,
+                                   const double* xs, const double2* lamv, double* partial, double* out, cudaStream_t st,
+                                   long long* nl) {
+    GreenPar p;
+    p.a = sqrt((lam + 2.0 * mu) / rho);
+    p.b = sqrt(mu / rho);
+    p.rho = rho;
+    p.w = omega;
+    p.mode = green;
+    long long nb = (d.N + 255) / 256;
+    if (nb > SG_BLOCKS) nb = SG_BLOCKS;
+    if (nb < 1) nb = 1;
+    k_source_grad<<<(int)nb, 256, 0, st>>>(d, p, xs[0], xs[1], xs[2], lamv, partial);
+    k_sum6<<<1, 32, 0, st>>>(partial, (int)nb, out);
+    if (nl) *nl += 2;
     return cudaGetLastError();
 }
 

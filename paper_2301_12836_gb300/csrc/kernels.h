@@ -60,6 +60,17 @@ template <typename T>
 cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* sys_dev, int nsys,
                            cudaStream_t st, long long* nlaunch);
 
+// Contrast gradient of Re<lam, K_T(Dv dC eps(u) + w^2 drho u)>: gC [21][N], grho [N] (FP64, device);
+// sys[0] supplies lam (as u), the spectrum, omega^2 and the workspaces.  accumulate adds to the outputs.
+cudaError_t launch_gradient(const Medium& m, const Plans& pl, const ApplySys<double>* sys, const double2* u, double* gC,
+                            double* grho, int accumulate, cudaStream_t st, long long* nl);
+
+// Moment-tensor gradient Re<lam, d u0 / d M_J>, J = 0..5 (Voigt), summed deterministically into out[6]
+// (device); partial is scratch of 6 * 4096 doubles.
+cudaError_t launch_source_gradient(const Dims& d, double lam, double mu, double rho, double omega, int green,
+                                   const double* xs, const double2* lamv, double* partial, double* out, cudaStream_t st,
+                                   long long* nl);
+
 // Green spectrum setup: writes the octant spectrum (double) scaled by 1/P into ghat64,
 // using scratch (6 * Lx*Ly*Lz complex double).  green: 0 exact, 1 paper.
 cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, double mu, double rho,

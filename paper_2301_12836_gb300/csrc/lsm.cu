@@ -67,6 +67,7 @@ struct Store {
     int* flag = nullptr;
     int* h_pinned = nullptr;   // pinned host ints for readbacks
     unsigned long long* counts = nullptr;  // device: executed system applies [FP64, FP32]
+    double* grad_scratch = nullptr;        // moment-gradient partial sums
     KTimer timer;
     SolverWS ws;
 };
@@ -139,7 +140,7 @@ void store_release(Store* s) {
     cudaFree(s->dC64); cudaFree(s->drho64); cudaFree(s->dC32); cudaFree(s->drho32);
     cudaFree(s->tw64); cudaFree(s->tw32);
     cudaFree(s->w1_64); cudaFree(s->w2_64); cudaFree(s->w1_32); cudaFree(s->w2_32);
-    cudaFree(s->a64); cudaFree(s->a32); cudaFree(s->flag); cudaFree(s->counts);
+    cudaFree(s->a64); cudaFree(s->a32); cudaFree(s->flag); cudaFree(s->counts); cudaFree(s->grad_scratch);
     if (s->timer.ev) {
         for (int i = 0; i < 2 * s->timer.cap; ++i) cudaEventDestroy(s->timer.ev[i]);
         delete[] s->timer.ev;
@@ -470,10 +471,17 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     return LSM_OK;
 }
 
+// A (adjoint = false) or A^H (adjoint = true) for nsys systems
+template <typename T>
+cudaError_t apply_op(bool adjoint, const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
+                     long long* nl) {
+    return adjoint ? launch_adjoint<T>(m, pl, sys, nsys, st, nl) : launch_apply<T>(m, pl, sys, nsys, st, nl);
+}
+
 // Run BiCGSTAB on nsys systems whose vectors/apply arguments are already on the device.
 template <typename T>
 lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const std::vector<double>& tol, int maxit,
-                        bool x_zero, const MixState* skip, std::vector<BcgState>& out) {
+                        bool x_zero, const MixState* skip, std::vector<BcgState>& out, bool adjoint) {
     Store* s = h0->s;
     SolverWS& w = s->ws;
     const long long n3 = w.n3;
@@ -500,7 +508,7 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
     CK(h0, cudaMemcpyAsync(w.st, init.data(), nsys * sizeof(BcgState), cudaMemcpyHostToDevice, st));
     CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
     if (!x_zero) {
-        cudaError_t e = launch_apply<T>(m, pl, sx, nsys, st, nl);
+        cudaError_t e = apply_op<T>(adjoint, m, pl, sx, nsys, st, nl);
         if (e != cudaSuccess) return cuda_fail(h0, e, "initial residual apply");
     }
     CK(h0, bcg_init<T>(vecs, w.st, pt, n3, nsys, x_zero ? 1 : 0, skip, w.n_active, st, nl));
@@ -510,11 +518,11 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
     int guard = 0;
     while (n_active > 0 && guard++ <= maxit + 1) {
         CK(h0, bcg_update_p<T>(vecs, w.st, n3, nsys, pt.nblk, st, nl));
-        cudaError_t e = launch_apply<T>(m, pl, sv, nsys, st, nl);
+        cudaError_t e = apply_op<T>(adjoint, m, pl, sv, nsys, st, nl);
         if (e != cudaSuccess) return cuda_fail(h0, e, "apply p");
         CK(h0, bcg_alpha<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
         CK(h0, bcg_s<T>(vecs, w.st, pt, n3, nsys, st, nl));
-        e = launch_apply<T>(m, pl, stt, nsys, st, nl);
+        e = apply_op<T>(adjoint, m, pl, stt, nsys, st, nl);
         if (e != cudaSuccess) return cuda_fail(h0, e, "apply s");
         CK(h0, bcg_omega<T>(vecs, w.st, pt, n3, nsys, st, nl));
         CK(h0, bcg_xr<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
@@ -531,8 +539,8 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
 
 }  // namespace
 
-extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void* const* b, void* const* x, int* iters,
-                                        double* relres, lsm_status* status) {
+static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const* b, void* const* x, int* iters,
+                                double* relres, lsm_status* status, bool adjoint) {
     if (nsys < 1 || !hs_in || !b || !x) return fail(nullptr, LSM_ERR_ARG, "lsm_solve_batched: bad arguments");
     std::vector<lsm_t> hs(hs_in, hs_in + nsys);
     for (int i = 0; i < nsys; ++i) {
@@ -587,7 +595,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
         CK(h0, cudaMemcpyAsync(w.sys_x, sx.data(), nsys * sizeof(sx[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys64, a64.data(), nsys * sizeof(a64[0]), cudaMemcpyHostToDevice, st));
         std::vector<BcgState> fin;
-        rc = run_bicgstab<double>(h0, hs, nsys, std::vector<double>(nsys, tol), h0->o.maxit, false, nullptr, fin);
+        rc = run_bicgstab<double>(h0, hs, nsys, std::vector<double>(nsys, tol), h0->o.maxit, false, nullptr, fin, adjoint);
         if (rc != LSM_OK) return rc;
         for (int i = 0; i < nsys; ++i) {
             it_out[i] = fin[i].iters;
@@ -597,7 +605,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
         }
         // true residual ||b - A x|| / ||b|| (Eq. 22)
         Medium m = medium_of(s, 0);
-        cudaError_t e = launch_apply<double>(m, s->pl64, w.sys64, nsys, st, &h0->nl);
+        cudaError_t e = apply_op<double>(adjoint, m, s->pl64, w.sys64, nsys, st, &h0->nl);
         if (e != cudaSuccess) return cuda_fail(h0, e, "final residual apply");
         void** P = w.ptrs;
         std::vector<void*> hp(6 * nsys);
@@ -666,7 +674,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
         const int nblk = pt.nblk;
         std::vector<double> itol(nsys, h0->o.inner_tol);
         for (int outer = 0;; ++outer) {
-            cudaError_t e = launch_apply<double>(m64, s->pl64, w.sys64, nsys, st, &h0->nl);
+            cudaError_t e = apply_op<double>(adjoint, m64, s->pl64, w.sys64, nsys, st, &h0->nl);
             if (e != cudaSuccess) return cuda_fail(h0, e, "FP64 residual apply");
             CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
             CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms,
@@ -686,7 +694,7 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
             CK(h0, mix_down((double2* const*)(P + 2 * nsys), (float2* const*)(P + 3 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
             for (int i = 0; i < nsys; ++i) CK(h0, cudaMemsetAsync(w.kry[i * KRY + 0], 0, n3 * sizeof(float2), st));
             std::vector<BcgState> fin;
-            rc = run_bicgstab<float>(h0, hs, nsys, itol, h0->o.maxit, true, w.ms, fin);
+            rc = run_bicgstab<float>(h0, hs, nsys, itol, h0->o.maxit, true, w.ms, fin, adjoint);
             if (rc != LSM_OK) return rc;
             for (int i = 0; i < nsys; ++i) it_out[i] += fin[i].iters;
             CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
@@ -711,11 +719,72 @@ extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs_in, const void
     return first;
 }
 
+extern "C" lsm_status lsm_solve_batched(int nsys, const lsm_t* hs, const void* const* b, void* const* x, int* iters,
+                                        double* relres, lsm_status* status) {
+    return solve_batched(nsys, hs, b, x, iters, relres, status, false);
+}
+
 extern "C" lsm_status lsm_solve(lsm_t h, const void* b, void* x, int* iters, double* relres) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_solve: null handle");
     const void* bb[1] = {b};
     void* xx[1] = {x};
-    return lsm_solve_batched(1, &h, bb, xx, iters, relres, nullptr);
+    return solve_batched(1, &h, bb, xx, iters, relres, nullptr, false);
+}
+
+extern "C" lsm_status lsm_solve_adjoint(lsm_t h, const void* b, void* x, int* iters, double* relres) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_solve_adjoint: null handle");
+    const void* bb[1] = {b};
+    void* xx[1] = {x};
+    return solve_batched(1, &h, bb, xx, iters, relres, nullptr, true);
+}
+
+extern "C" lsm_status lsm_set_contrast(lsm_t h, const double* dC, const double* drho) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_set_contrast: null handle");
+    if (!dC || !drho) return fail(h, LSM_ERR_ARG, "lsm_set_contrast: null pointer argument");
+    Store* s = h->s;
+    const long long N = s->d.N;
+    CK(h, cudaMemcpyAsync(s->dC64, dC, 21 * N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CK(h, cudaMemcpyAsync(s->drho64, drho, N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    if (s->precision == LSM_MIXED) {
+        CK(h, launch_d2f(s->dC64, s->dC32, 21 * N, s->st, &h->nl));
+        CK(h, launch_d2f(s->drho64, s->drho32, N, s->st, &h->nl));
+    }
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_gradient(lsm_t h, const void* u, const void* lam, double* gC, double* grho, int accumulate) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_gradient: null handle");
+    if (!u || !lam || !gC || !grho) return fail(h, LSM_ERR_ARG, "lsm_gradient: null pointer argument");
+    Store* s = h->s;
+    lsm_status rc = ensure_apply_ws(h);
+    if (rc != LSM_OK) return rc;
+    ApplySys<double> a;
+    a.u = (const double2*)lam;
+    a.out = nullptr;
+    a.ghat = h->ghat64;
+    a.w1 = s->w1_64;
+    a.w2 = s->w2_64;
+    a.omega2 = h->omega * h->omega;
+    a.run = nullptr;
+    a.count = nullptr;
+    CK(h, cudaMemcpyAsync(s->a64, &a, sizeof(a), cudaMemcpyHostToDevice, s->st));
+    Medium m = medium_of(s, 0);
+    m.timer = nullptr;
+    CK(h, launch_gradient(m, s->pl64, s->a64, (const double2*)u, gC, grho, accumulate, s->st, &h->nl));
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const void* lam, double gM[6]) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_source_gradient: null handle");
+    if (!xs || !lam || !gM) return fail(h, LSM_ERR_ARG, "lsm_source_gradient: null pointer argument");
+    Store* s = h->s;
+    if (!s->grad_scratch) CK(h, cudaMalloc(&s->grad_scratch, (6 * 4096 + 8) * sizeof(double)));
+    double* out = s->grad_scratch + 6 * 4096;
+    CK(h, launch_source_gradient(s->d, s->lam, s->mu, s->rho, h->omega, s->green, xs, (const double2*)lam,
+                                 s->grad_scratch, out, s->st, &h->nl));
+    CK(h, cudaMemcpyAsync(gM, out, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(h, cudaStreamSynchronize(s->st));
+    return LSM_OK;
 }
 
 extern "C" lsm_status lsm_timer_start(lsm_t h, int enable) {

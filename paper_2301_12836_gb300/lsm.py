@@ -33,7 +33,8 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_apply", "lsm_apply_c64",
-           "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
+           "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
+           "lsm_source_gradient", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
 
@@ -76,6 +77,14 @@ def load(path: str = LIB_PATH):
     lib.lsm_solve_batched.argtypes = [i, ct.POINTER(vp), ct.POINTER(vp), ct.POINTER(vp), ct.POINTER(i),
                                       ct.POINTER(d), ct.POINTER(i)]
     lib.lsm_solve_batched.restype = i
+    lib.lsm_solve_adjoint.argtypes = [vp, vp, vp, ct.POINTER(i), ct.POINTER(d)]
+    lib.lsm_solve_adjoint.restype = i
+    lib.lsm_set_contrast.argtypes = [vp, vp, vp]
+    lib.lsm_set_contrast.restype = i
+    lib.lsm_gradient.argtypes = [vp, vp, vp, vp, vp, i]
+    lib.lsm_gradient.restype = i
+    lib.lsm_source_gradient.argtypes = [vp, ct.POINTER(d), vp, ct.POINTER(d)]
+    lib.lsm_source_gradient.restype = i
     lib.lsm_launch_count.argtypes = [vp]
     lib.lsm_launch_count.restype = ct.c_longlong
     lib.lsm_timer_start.argtypes = [vp, i]
@@ -204,6 +213,35 @@ def lsm_solve_batched(hs, bs, xs, check=True):
     if check:
         _check(code, hs[0].ptr)
     return code, list(it), list(rr), list(stt)
+
+
+def lsm_solve_adjoint(h: Handle, b: torch.Tensor, x: torch.Tensor, check=True):
+    """Solve A^H x = b.  Returns (status, iterations, relres)."""
+    it = ct.c_int(0)
+    rr = ct.c_double(0.0)
+    code = load().lsm_solve_adjoint(h.ptr, _ptr(b, torch.complex128, 3 * h.N), _ptr(x, torch.complex128, 3 * h.N),
+                                    ct.byref(it), ct.byref(rr))
+    if check:
+        _check(code, h.ptr)
+    return code, it.value, rr.value
+
+
+def lsm_set_contrast(h: Handle, dC: torch.Tensor, drho: torch.Tensor) -> None:
+    _check(load().lsm_set_contrast(h.ptr, _ptr(dC, torch.float64, 21 * h.N), _ptr(drho, torch.float64, h.N)), h.ptr)
+
+
+def lsm_gradient(h: Handle, u: torch.Tensor, lam: torch.Tensor, gC: torch.Tensor, grho: torch.Tensor,
+                 accumulate: bool = False) -> None:
+    _check(load().lsm_gradient(h.ptr, _ptr(u, torch.complex128, 3 * h.N), _ptr(lam, torch.complex128, 3 * h.N),
+                               _ptr(gC, torch.float64, 21 * h.N), _ptr(grho, torch.float64, h.N),
+                               1 if accumulate else 0), h.ptr)
+
+
+def lsm_source_gradient(h: Handle, xs, lam: torch.Tensor):
+    x = (ct.c_double * 3)(*[float(v) for v in xs])
+    g = (ct.c_double * 6)()
+    _check(load().lsm_source_gradient(h.ptr, x, _ptr(lam, torch.complex128, 3 * h.N), g), h.ptr)
+    return list(g)
 
 
 def lsm_launch_count(h: Handle) -> int:

@@ -1,0 +1,142 @@
+"""Adjoint solve and gradients on the GPU (through the C ABI) against the oracle and finite differences.
+
+Tolerances: adjoint solve 1e-10 (both sides to relres 1e-12); contrast and moment gradients
+from the same u and lambda 1e-11 relative; end-to-end autograd gradients vs central finite
+differences 1e-6 relative (FP64 solves to 1e-12, step 1e-3 of a unit-scale direction).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as sy
+from oracle import operator as op, solver as osv, source as osrc
+from paper_2301_12836_gb300 import lsm
+from paper_2301_12836_gb300.autograd import ReceiverModel
+
+from gpu_helpers import dev, field, handle, host, rel
+
+pytestmark = pytest.mark.gpu
+
+W = 2 * np.pi * 11.0
+
+
+def test_adjoint_solve_parity():
+    med = sy.random_medium((10, 8, 12), h=10.0, seed=51, frac=0.1)
+    h = handle(med, W, tol=1e-12)
+    b = field(med.shape, 52)
+    x = torch.zeros(3 * h.N, dtype=torch.complex128, device="cuda")
+    code, it, rr = lsm.lsm_solve_adjoint(h, dev(b).reshape(-1), x)
+    assert code == lsm.LSM_OK and rr <= 1e-12
+    F = op.FFTOperator(med, W)
+    xo, *_ = osv.bicgstab(F.adjoint, b, tol=1e-13, maxit=500)
+    assert rel(host(x).reshape(b.shape), xo) < 1e-10
+    # and it differs from the forward solve (A is not Hermitian)
+    xf, *_ = osv.bicgstab(F.apply, b, tol=1e-13, maxit=500)
+    assert rel(xf, xo) > 1e-3
+
+
+@pytest.mark.parametrize("n", [(9, 8, 10), (16, 16, 16)])
+def test_gradient_kernels_parity(n):
+    med = sy.random_medium(n, h=8.0, seed=53, frac=0.1)
+    h = handle(med, W)
+    u = field(med.shape, 54)
+    lam = field(med.shape, 55)
+    N = h.N
+    gC = torch.zeros(21 * N, dtype=torch.float64, device="cuda")
+    grho = torch.zeros(N, dtype=torch.float64, device="cuda")
+    lsm.lsm_gradient(h, dev(u).reshape(-1), dev(lam).reshape(-1), gC, grho)
+    wC, wr = op.contrast_gradient(u, lam, med, W)
+    assert rel(host(gC).reshape(wC.shape), wC) < 1e-11
+    assert rel(host(grho).reshape(wr.shape), wr) < 1e-11
+    # accumulate adds
+    lsm.lsm_gradient(h, dev(u).reshape(-1), dev(lam).reshape(-1), gC, grho, accumulate=True)
+    assert rel(host(gC).reshape(wC.shape), 2 * wC) < 1e-11
+    xs = np.array([31.0, 27.0, 40.0])
+    gM = lsm.lsm_source_gradient(h, xs, dev(lam).reshape(-1))
+    wM = osrc.moment_gradient(lam, med.n, med.h, xs, W, med.lam0, med.mu0, med.rho0)
+    assert np.abs(np.array(gM) - wM).max() < 1e-11 * np.abs(wM).max()
+
+
+def _model(med, freqs, xs, rec):
+    dC = dev(med.dC)
+    drho = dev(med.drho)
+    return ReceiverModel(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, freqs, xs, rec, tol=1e-12)
+
+
+@pytest.mark.parametrize("shape,freqs,seed", [((12, 10, 15), (6.0, 13.0), 56), ((16, 16, 16), (9.0,), 57)])
+def test_autograd_gradient_vs_finite_differences_and_oracle(shape, freqs, seed):
+    med = sy.random_medium(shape, h=10.0, seed=seed, frac=0.08)
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    rec = np.stack([rng.integers(0, nx, 6), rng.integers(0, ny, 6), rng.integers(0, nz, 6)], axis=1)
+    xs = np.array([(nx - 1) * 5.0 + 1.3, (ny - 1) * 5.0 - 2.1, (nz - 1) * 5.0 + 0.7])
+    model = _model(med, freqs, xs, rec)
+    dobs = torch.from_numpy(rng.standard_normal((len(freqs), 6, 3)) + 1j * rng.standard_normal((len(freqs), 6, 3))).cuda() * 1e-12
+    dC = dev(med.dC).requires_grad_(True)
+    drho = dev(med.drho).requires_grad_(True)
+    M = torch.tensor(rng.standard_normal(6), dtype=torch.float64, requires_grad=True)
+
+    def loss(dC_, drho_, M_):
+        d = model(dC_, drho_, M_)
+        return 0.5 * torch.sum(torch.abs(d - dobs) ** 2)
+
+    L = loss(dC, drho, M)
+    L.backward()
+    gC, gr, gM = dC.grad.detach(), drho.grad.detach(), M.grad.detach()
+    for trial in range(2):
+        vC = torch.from_numpy(rng.standard_normal(med.dC.shape) * 1e8).cuda()
+        vr = torch.from_numpy(rng.standard_normal(med.drho.shape) * 20.0).cuda()
+        vM = torch.tensor(rng.standard_normal(6))
+        e = 1e-3
+        with torch.no_grad():
+            Lp = loss(dC + e * vC, drho + e * vr, M + e * vM)
+            Lm = loss(dC - e * vC, drho - e * vr, M - e * vM)
+        fd = float((Lp - Lm) / (2 * e))
+        an = float(torch.sum(gC * vC) + torch.sum(gr * vr) + torch.sum(gM * vM))
+        assert abs(fd - an) <= 1e-6 * abs(an), (trial, fd, an)
+    # with one frequency, the oracle's discrete adjoint gives the same contrast gradients
+    if len(freqs) == 1:
+        w = 2 * np.pi * freqs[0]
+        F = op.FFTOperator(med, w)
+        u0, _ = osrc.background_field(med.n, med.h, M.detach().numpy(), xs, w, med.lam0, med.mu0, med.rho0)
+        u, *_ = osv.bicgstab(F.apply, u0, tol=1e-13, maxit=500)
+        d = u[:, rec[:, 2], rec[:, 1], rec[:, 0]]
+        g = (d - dobs[0].cpu().numpy().T)
+        rhs = np.zeros_like(u)
+        rhs[:, rec[:, 2], rec[:, 1], rec[:, 0]] = g
+        lam, *_ = osv.bicgstab(F.adjoint, rhs, tol=1e-13, maxit=500)
+        wC, wr = op.contrast_gradient(u, lam, med, w)
+        assert rel(host(gC).reshape(wC.shape), wC) < 1e-8
+        assert rel(host(gr).reshape(wr.shape), wr) < 1e-8
+
+
+@pytest.mark.slow
+def test_adjoint_workload_96_surface_receivers():
+    """96^3 Table-2 layers + 3% random perturbation, dip-slip source, 256 surface receivers
+    (x, y in {3 + 6k}), two of the workload's frequencies: gradient vs central differences."""
+    wl = sy.get_workload("table2_96_adjoint")
+    med = wl.medium()
+    M0, xs = wl.sources()
+    ks = 3 + 6 * np.arange(16)
+    rec = np.array([[x, y, 0] for y in ks for x in ks])
+    freqs = wl.freqs_hz[:2]
+    model = _model(med, freqs, xs[0], rec)
+    rng = np.random.default_rng(96)
+    dC = dev(med.dC).requires_grad_(True)
+    drho = dev(med.drho).requires_grad_(True)
+    M = torch.tensor(M0[0], dtype=torch.float64, requires_grad=True)
+    with torch.no_grad():
+        dobs = 1.05 * model(dC, drho, M)       # synthetic "observed" data: a perturbed copy
+    def loss(a, b, c):
+        return 0.5 * torch.sum(torch.abs(model(a, b, c) - dobs) ** 2)
+    L = loss(dC, drho, M)
+    L.backward()
+    for trial in range(2):
+        vC = torch.from_numpy(rng.standard_normal(med.dC.shape) * 1e8).cuda()
+        vr = torch.from_numpy(rng.standard_normal(med.drho.shape) * 20.0).cuda()
+        vM = torch.tensor(rng.standard_normal(6))
+        e = 1e-3
+        with torch.no_grad():
+            fd = float((loss(dC + e * vC, drho + e * vr, M + e * vM) - loss(dC - e * vC, drho - e * vr, M - e * vM)) / (2 * e))
+        an = float(torch.sum(dC.grad * vC) + torch.sum(drho.grad * vr) + torch.sum(M.grad * vM))
+        assert abs(fd - an) <= 1e-5 * abs(an), (trial, fd, an)
