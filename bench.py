@@ -213,6 +213,25 @@ def oracle_apply_sample(med, omega, reps=1):
     return setup, times
 
 
+def rank_frequencies(rank, world, steps_total, nfreq):
+    """Frequencies (indices) a rank solves, one per step: ranks take disjoint consecutive blocks
+    (weak scaling: every rank does the same work; no data is exchanged between ranks)."""
+    return [(rank * steps_total + s) % nfreq for s in range(steps_total)]
+
+
+def reduce_timing(ms, applies, solves, launches, world, dist=None, device="cpu"):
+    """Whole-job totals: the slowest rank's time, the sums of the work counters."""
+    import torch
+    t = torch.tensor([ms, applies, solves, launches], dtype=torch.float64, device=device)
+    if world > 1:
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t[1:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        return float(mx[0]), float(sm[0]), float(sm[1]), float(sm[2])
+    return float(t[0]), float(t[1]), float(t[2]), float(t[3])
+
+
 def workload_inputs(args):
     import synthetic as sy
     wl = sy.get_workload(args.workload)
@@ -286,7 +305,7 @@ def main():
     steps_total = args.warmup + args.steps
     freqs = list(wl.freqs_hz)
     # weak scaling: rank r takes its own frequencies
-    fidx = [(rank * steps_total + s) % len(freqs) for s in range(steps_total)]
+    fidx = rank_frequencies(rank, world, steps_total, len(freqs))
     dC = torch.from_numpy(med.dC).cuda().contiguous()
     drho = torch.from_numpy(med.drho).cuda().contiguous()
     opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000)
@@ -352,15 +371,7 @@ def main():
     launches = sum(lsm.lsm_launch_count(h) for h in handles.values()) - launches0
     solves = args.steps * nsys
     applies = a64 + a32
-    tot = torch.tensor([ms, applies, solves, launches], dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = tot[:1].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot[1:].clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, applies_all, solves_all, launches_all = float(mx[0]), *[float(v) for v in sm]
-    else:
-        ms_max, applies_all, solves_all, launches_all = ms, float(applies), float(solves), float(launches)
+    ms_max, applies_all, solves_all, launches_all = reduce_timing(ms, applies, solves, launches, world, dist, "cuda")
     value = applies_all / (ms_max / 1e3)
     # per-stage rooflines: FP32 stages against HBM (algorithmic bytes), FP64 stages against the
     # FP64 pipe (model flops); the dominant stage (largest share of the timed region) is reported

@@ -71,6 +71,10 @@ typedef struct {
                           Each inner solve aims at 0.1 * tol / (current FP64 relres),
                           clamped to [inner_tol, 0.1] (default 1e-6) */
     int max_outer;     /* mixed: refinement steps limit (default 8) */
+    int taper;         /* absorbing boundary (Eq. 25): width in nodes of the layer in which the
+                          contrast sources are weighted by prod_a [1 - exp(-l_a^2 / (N_a dx^2))],
+                          l_a = distance to the outer node plane along axis a, N_a = nodes along a;
+                          0 = none (default) */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */
@@ -202,6 +206,20 @@ lsm_status lsm_gradient(lsm_t h, const void *u, const void *lam, double *gC, dou
  *   lam  device complex128, 3 * nz*ny*nx;  gM  host double[6] (written).  Synchronises the stream.
  */
 lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const void *lam, double gM[6]);
+
+/*
+ * Receiver time traces from frequency-domain receiver data (Sec. 4.1.2: solve at the positive and
+ * negative frequencies up to Nyquist, inverse Fourier transform).  With exp(-i w t) and a real
+ * medium U(-f) = conj(U(f)), so positive frequencies f_k = k df (k = 0..nf-1) suffice:
+ *   u(t_j) = df [W_0 U_0 + 2 Re sum_{k>=1} W_k U_k exp(-2 pi i f_k t_j)],  t_j = j dt,
+ * W_k the Ricker spectrum 2 f^2/(sqrt(pi) fp^3) exp(-f^2/fp^2) exp(+2 pi i f t0).
+ *   nf       1..12288 frequencies;  df  spacing [Hz]
+ *   ntr      traces (e.g. receivers x 3 components);  spectra  device complex128 [nf][ntr]
+ *   nt, dt   samples and interval [s];  fp  Ricker peak frequency [Hz];  t0  delay [s]
+ *   traces   device float64 [ntr][nt] (written);  stream  cudaStream_t (as void*)
+ */
+lsm_status lsm_time_traces(int nf, double df, int ntr, const void *spectra, int nt, double dt, double fp, double t0,
+                           double *traces, void *stream);
 
 /* Number of kernel launches the library has issued on this handle (diagnostics). */
 long long lsm_launch_count(lsm_t h);

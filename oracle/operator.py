@@ -412,3 +412,33 @@ def contrast_gradient(u, lam, medium, omega, mode="exact"):
     zin = z[:, 1:-1, 1:-1, 1:-1]
     grho = omega ** 2 * np.real(np.sum(np.conj(zin) * u, axis=0))
     return gC, grho
+
+
+def taper_weight(n, h, width):
+    """Absorbing-boundary weight of Eq. 25 on the model's nodes, shape (nz, ny, nx).
+
+    Reading of Eq. 25: inside a boundary layer of `width` nodes the contrast sources are
+    multiplied by 1 - exp(-l^2 / (N_a h^2)) for each axis a whose layer contains the node, with
+    l the distance from the node to the model's outer boundary node plane along that axis and
+    N_a the number of nodes along it; outside the layer the factor is 1.  width = 0: no taper.
+    """
+    out = np.ones(tuple(reversed(n)))
+    if width <= 0:
+        return out
+    factors = []
+    for a, N in enumerate(n):
+        k = np.arange(N)
+        dist = np.minimum(k, N - 1 - k)
+        f = np.where(dist < width, 1.0 - np.exp(-(dist * h) ** 2 / (N * h * h)), 1.0)
+        factors.append(f)
+    return factors[2][:, None, None] * factors[1][None, :, None] * factors[0][None, None, :]
+
+
+def tapered(medium, width):
+    """The medium with its contrasts weighted by ``taper_weight`` (Eq. 25)."""
+    import copy
+    w = taper_weight(medium.n, medium.h, width)
+    m = copy.copy(medium)
+    m.dC = medium.dC * w[None]
+    m.drho = medium.drho * w
+    return m

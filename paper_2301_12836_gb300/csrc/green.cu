@@ -275,6 +275,36 @@ cudaError_t launch_source_gradient(const Dims& d, double lam, double mu, double 
     return cudaGetLastError();
 }
 
+// Eq. 25: inside a layer of `width` nodes each axis contributes 1 - exp(-l^2 / (N h^2)), l the
+// distance to the outer node plane along that axis, N the nodes along it.
+__device__ __forceinline__ double taper_factor(int k, int N, double h, int width) {
+    const int dist = k < N - 1 - k ? k : N - 1 - k;
+    if (dist >= width) return 1.0;
+    const double l = dist * h;
+    return 1.0 - exp(-l * l / ((double)N * h * h));
+}
+
+__global__ void k_taper(Dims d, int width, double* __restrict__ dC, double* __restrict__ drho) {
+    const long long N = d.N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % d.nx);
+        const int iy = (int)((i / d.nx) % d.ny);
+        const int iz = (int)(i / ((long long)d.nx * d.ny));
+        const double w = taper_factor(ix, d.nx, d.h, width) * taper_factor(iy, d.ny, d.h, width) *
+                         taper_factor(iz, d.nz, d.h, width);
+        if (w == 1.0) continue;
+        for (int k = 0; k < 21; ++k) dC[k * N + i] *= w;
+        drho[i] *= w;
+    }
+}
+
+cudaError_t launch_taper(const Dims& d, int width, double* dC, double* drho, cudaStream_t st, long long* nl) {
+    if (width <= 0) return cudaSuccess;
+    k_taper<<<gsz(d.N), 256, 0, st>>>(d, width, dC, drho);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
 __global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = (float)in[i];

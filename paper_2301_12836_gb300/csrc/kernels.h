@@ -82,6 +82,13 @@ cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, doub
                           const double* M6, const double* xs, double2* u0, int* flag,
                           cudaStream_t st, long long* nlaunch);
 
+// Absorbing-boundary weight (Eq. 25) applied in place to the 21 contrast planes and drho (FP64).
+cudaError_t launch_taper(const Dims& d, int width, double* dC, double* drho, cudaStream_t st, long long* nl);
+
+// Receiver time traces (Ricker wavelet, real-signal inverse Fourier sum), FP64.
+cudaError_t launch_time_traces(int nf, double df, int ntr, const double2* U, int nt, double dt, double fp, double t0,
+                               double* out, cudaStream_t st);
+
 // Precision converters.
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t st, long long* nlaunch);
 cudaError_t launch_f2d_c(const float2* in, double2* out, long long n, cudaStream_t st, long long* nlaunch);

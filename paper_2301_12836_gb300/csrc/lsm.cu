@@ -51,6 +51,7 @@ struct Store {
     Dims d;
     double lam = 0, mu = 0, rho = 0;
     int precision = LSM_FP64, green = LSM_GREEN_EXACT;
+    int taper = 0;
     cudaStream_t st = nullptr;
     double* dC64 = nullptr;
     double* drho64 = nullptr;
@@ -185,6 +186,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->maxit = 1000;
     o->inner_tol = 1e-6;
     o->max_outer = 8;
+    o->taper = 0;
 }
 
 static lsm_status build_spectrum(lsm_t h) {
@@ -221,7 +223,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     lsm_default_opts(&o);
     if (opts) o = *opts;
     if ((o.precision != LSM_FP64 && o.precision != LSM_MIXED) || (o.green != LSM_GREEN_EXACT && o.green != LSM_GREEN_PAPER) ||
-        !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1)
+        !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1 || o.taper < 0)
         return fail(nullptr, LSM_ERR_ARG, "lsm_create: invalid options");
     static bool attrs_done = false;
     if (!attrs_done) {
@@ -272,6 +274,8 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     CKB(cudaMalloc(&s->drho64, d.N * sizeof(double)));
     CKB(cudaMemcpyAsync(s->dC64, dC, 21 * d.N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CKB(cudaMemcpyAsync(s->drho64, drho, d.N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    s->taper = o.taper;
+    CKB(launch_taper(d, s->taper, s->dC64, s->drho64, s->st, &h->nl));
     if (o.precision == LSM_MIXED) {
         CKB(cudaMalloc(&s->dC32, 21 * d.N * sizeof(float)));
         CKB(cudaMalloc(&s->drho32, d.N * sizeof(float)));
@@ -745,6 +749,7 @@ extern "C" lsm_status lsm_set_contrast(lsm_t h, const double* dC, const double* 
     const long long N = s->d.N;
     CK(h, cudaMemcpyAsync(s->dC64, dC, 21 * N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CK(h, cudaMemcpyAsync(s->drho64, drho, N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    CK(h, launch_taper(s->d, s->taper, s->dC64, s->drho64, s->st, &h->nl));
     if (s->precision == LSM_MIXED) {
         CK(h, launch_d2f(s->dC64, s->dC32, 21 * N, s->st, &h->nl));
         CK(h, launch_d2f(s->drho64, s->drho32, N, s->st, &h->nl));
@@ -917,5 +922,15 @@ extern "C" lsm_status lsm_apply_static(lsm_t h, const void* u, void* Au) {
     m.timer = nullptr;
     cudaError_t e = launch_apply<double>(m, s->pl64, dev_args, 1, s->st, &h->nl);
     if (e != cudaSuccess) return cuda_fail(h, e, "lsm_apply_static");
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_time_traces(int nf, double df, int ntr, const void* spectra, int nt, double dt, double fp,
+                                      double t0, double* traces, void* stream) {
+    if (nf < 1 || nf > 12288 || ntr < 1 || nt < 1 || !spectra || !traces || !(df > 0) || !(dt > 0) || !(fp > 0) ||
+        !std::isfinite(t0))
+        return fail(nullptr, LSM_ERR_ARG, "lsm_time_traces: need 1 <= nf <= 12288, ntr, nt >= 1, df, dt, fp > 0");
+    cudaError_t e = launch_time_traces(nf, df, ntr, (const double2*)spectra, nt, dt, fp, t0, traces, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lsm_time_traces");
     return LSM_OK;
 }

@@ -34,13 +34,13 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_apply", "lsm_apply_c64",
            "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
-           "lsm_source_gradient", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
+           "lsm_source_gradient", "lsm_time_traces", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
 
 class lsm_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("green", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
-                ("inner_tol", ct.c_double), ("max_outer", ct.c_int)]
+                ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int)]
 
 
 class LSMError(RuntimeError):
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.lsm_gradient.restype = i
     lib.lsm_source_gradient.argtypes = [vp, ct.POINTER(d), vp, ct.POINTER(d)]
     lib.lsm_source_gradient.restype = i
+    lib.lsm_time_traces.argtypes = [i, d, i, vp, i, d, d, d, vp, vp]
+    lib.lsm_time_traces.restype = i
     lib.lsm_launch_count.argtypes = [vp]
     lib.lsm_launch_count.restype = ct.c_longlong
     lib.lsm_timer_start.argtypes = [vp, i]
@@ -242,6 +244,16 @@ def lsm_source_gradient(h: Handle, xs, lam: torch.Tensor):
     g = (ct.c_double * 6)()
     _check(load().lsm_source_gradient(h.ptr, x, _ptr(lam, torch.complex128, 3 * h.N), g), h.ptr)
     return list(g)
+
+
+def lsm_time_traces(spectra: torch.Tensor, df, nt, dt, fp, t0, stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """spectra: device complex128 (nf, ntr) at f_k = k df -> device float64 traces (ntr, nt)."""
+    nf, ntr = spectra.shape
+    out = torch.empty((ntr, nt), dtype=torch.float64, device=spectra.device)
+    st = (stream or torch.cuda.current_stream(spectra.device)).cuda_stream
+    _check(load().lsm_time_traces(int(nf), float(df), int(ntr), _ptr(spectra, torch.complex128, nf * ntr), int(nt),
+                                  float(dt), float(fp), float(t0), _ptr(out, torch.float64, ntr * nt), ct.c_void_p(st)))
+    return out
 
 
 def lsm_launch_count(h: Handle) -> int:

@@ -47,7 +47,7 @@ def test_default_opts(lib):
     from paper_2301_12836_gb300 import lsm
     o = lsm.lsm_default_opts()
     assert o.precision == lsm.LSM_FP64 and o.green == lsm.LSM_GREEN_EXACT
-    assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-6 and o.max_outer >= 2
+    assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-6 and o.max_outer >= 2 and o.taper == 0
 
 
 @pytest.mark.parametrize("n,ok", [((2, 2, 2), True), ((1, 4, 4), False), ((7, 4, 4), False),
@@ -89,7 +89,8 @@ def test_bad_options_rejected(lib):
     out = ct.c_void_p()
     arr = (ct.c_int * 3)(4, 4, 4)
     fake = ct.c_void_p(16)
-    for kw in (dict(precision=7), dict(green=3), dict(tol=0.0), dict(maxit=0), dict(inner_tol=-1.0), dict(max_outer=0)):
+    for kw in (dict(precision=7), dict(green=3), dict(tol=0.0), dict(maxit=0), dict(inner_tol=-1.0), dict(max_outer=0),
+               dict(taper=-2)):
         o = lsm.lsm_default_opts(**kw)
         code = lib.lsm_create(ct.byref(out), arr, 10.0, 1e9, 1e9, 2000.0, fake, fake, 1.0, ct.byref(o), None)
         assert code == lsm.LSM_ERR_ARG, kw

@@ -197,3 +197,33 @@ def test_solve_zero_rhs_and_noconv():
     u0 = host(b).reshape(3, 8, 8, 8)
     rr_o = osv.relres(op.FFTOperator(med, W).apply, u0, host(x).reshape(u0.shape))
     assert abs(rr_o - rr) < 1e-12 and rr < 1.0
+
+
+@pytest.mark.parametrize("precision", [lsm.LSM_FP64, lsm.LSM_MIXED])
+def test_taper_parity(precision):
+    """Eq. 25 absorbing taper applied by the library equals the oracle operator of the tapered medium,
+    also after lsm_set_contrast."""
+    med = sy.random_medium((16, 12, 10), h=8.0, seed=63, frac=0.2)
+    h = handle(med, W, precision=precision, taper=4)
+    t = op.tapered(med, 4)
+    u = field(med.shape, 64)
+    Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_apply(h, dev(u).reshape(-1), Au)
+    want = op.FFTOperator(t, W).apply(u)
+    assert rel(host(Au).reshape(u.shape), want) < 1e-12
+    med2 = sy.random_medium((16, 12, 10), h=8.0, seed=65, frac=0.2)
+    lsm.lsm_set_contrast(h, dev(med2.dC), dev(med2.drho))
+    lsm.lsm_apply(h, dev(u).reshape(-1), Au)
+    want2 = op.FFTOperator(op.tapered(med2, 4), W).apply(u)
+    assert rel(host(Au).reshape(u.shape), want2) < 1e-12
+
+
+def test_time_traces_parity():
+    """Receiver traces (Ricker, inverse Fourier sum over +-f) against the oracle's synthesis."""
+    from oracle import synthesis as osyn
+    rng = np.random.default_rng(66)
+    nf, ntr, nt, dt, df = 300, 7, 400, 3e-4, 1.25
+    U = rng.standard_normal((nf, ntr)) + 1j * rng.standard_normal((nf, ntr))
+    got = lsm.lsm_time_traces(dev(U), df, nt, dt, 60.0, 0.03)
+    want = osyn.traces(U, df, nt, dt, 60.0, 0.03)
+    assert np.abs(host(got) - want.reshape(ntr, nt)).max() < 1e-12 * np.abs(want).max()

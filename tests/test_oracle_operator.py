@@ -274,3 +274,34 @@ def test_apply_at_points_equals_fft_form():
     got = op.apply_at_points(u, med, W10, pts)
     for (ix, iy, iz), g in zip(pts, got):
         assert np.abs(g - full[:, iz, iy, ix]).max() < 1e-13 * np.abs(full).max()
+
+
+def test_taper_weight_properties():
+    """Eq. 25's weight: zero on the outer node planes, 1 beyond the layer, symmetric, separable,
+    increasing inward, and 1 - exp(-l^2 / (N h^2)) on a single-axis profile."""
+    n, h, width = (20, 12, 16), 7.0, 5
+    w = op.taper_weight(n, h, width)
+    assert w.shape == (16, 12, 20)
+    assert np.all(w[0] == 0) and np.all(w[:, :, -1] == 0) and np.all(w[:, 0, :] == 0)
+    assert np.all(w[5:-5, 5:-5, 5:-5] == 1.0)
+    assert np.allclose(w, w[::-1, ::-1, ::-1])
+    prof = w[8, 6, :]
+    assert np.all(np.diff(prof[:6]) > 0) and prof[5] == 1.0
+    k = np.arange(5)
+    assert np.allclose(prof[:5], 1 - np.exp(-(k * h) ** 2 / (20 * h * h)))
+    # separable: w = w_x w_y w_z
+    assert np.allclose(w[2, 3, 4], w[2, 6, 10] * w[8, 3, 10] * w[8, 6, 4])
+    assert np.array_equal(op.taper_weight(n, h, 0), np.ones((16, 12, 20)))
+
+
+def test_taper_zeroes_boundary_contrast_sources():
+    """With the taper a contrast that touches the boundary contributes nothing on the outer planes:
+    the operator equals that of the medium whose boundary-node contrast is zero there."""
+    med = sy.random_medium((8, 7, 9), h=10.0, seed=61, frac=0.2)
+    t = op.tapered(med, 3)
+    assert np.all(t.dC[:, 0] == 0) and np.all(t.drho[:, :, -1] == 0)
+    assert np.allclose(t.dC[:, 4, 3, 4], med.dC[:, 4, 3, 4])
+    u = _field(med.shape, 62)
+    a = op.FFTOperator(t, W10).apply(u)
+    b = (op.dense_matrix(t, W10) @ u.reshape(-1)).reshape(u.shape)
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-13
