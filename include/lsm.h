@@ -75,6 +75,11 @@ typedef struct {
                           contrast sources are weighted by prod_a [1 - exp(-l_a^2 / (N_a dx^2))],
                           l_a = distance to the outer node plane along axis a, N_a = nodes along a;
                           0 = none (default) */
+    int graph;         /* 1 (default): the BiCGSTAB iteration kernels of a solve are captured once
+                          into a CUDA graph (two iterations per graph, kernels of stopped systems
+                          return at once) and replayed, one host synchronisation per replay;
+                          the graph is kept with the solver workspace and reused by later solves
+                          of the same batch size.  0: every kernel is launched from the host. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */
@@ -126,6 +131,19 @@ lsm_status lsm_create_shared(lsm_t *out, lsm_t base, double omega);
  * the handle's stream to read that flag.
  */
 lsm_status lsm_source(lsm_t h, const double M[6], const double xs[3], void *u0);
+
+/*
+ * Background fields of nm moment tensors at one source position (Eqs. 13-16),
+ * as nm calls of lsm_source would give them; the Green's-tensor derivative
+ * (the transcendental part) is evaluated once per node for all of them.
+ *   nm  1 .. 4096
+ *   M   host double[6 * nm], tensor m at M[6m .. 6m+5] in lsm_source's order
+ *   xs  host double[3], source position [m]
+ *   u0  host array of nm device pointers, each complex128 3 * nz*ny*nx (written)
+ * LSM_ERR_ARG for nm out of range, a null pointer or a non-finite input;
+ * LSM_WARN_SOURCE_ON_NODE as for lsm_source.  Synchronises the stream once.
+ */
+lsm_status lsm_source_moments(lsm_t h, int nm, const double *M, const double xs[3], void *const *u0);
 
 /*
  * One application of the LS operator (Eqs. 19-21): Au = A u in FP64.

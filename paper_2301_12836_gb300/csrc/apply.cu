@@ -245,7 +245,7 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const ty
         const int eo = k - out_off;
         if (xin && eo >= 0 && eo < out_count) dst[eo * des] = v;
     };
-    fft4_io<A, B, DIR, false, false, TX>(s, tw, threadIdx.x, ld, st);
+    fft4_io<A, B, DIR, false, false, TX>(s, tw, threadIdx.x, ld, st, in_off + in_count);
 }
 
 // four-step z pass with the Green multiply.  Block = 3 TX * TPL threads; line l = c * TX + lx.
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(
     const int ky = blockIdx.y;
     const int x0 = blockIdx.x * TX;
     const int fy = ky <= d.ny ? ky : d.Ly - ky;
-    const R sy = ky > d.ny ? (R)-1 : (R)1;
+    const unsigned my = ky > d.ny ? SIGN_BIT : 0u;
     const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const int plane = d.Ly * d.Lx;
     // this thread's line (fixed through both FFTs): component cl, column x0 + lxl
@@ -321,25 +321,19 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(
             const int kx = x0 + lx;
             if (kx >= d.Lx) continue;
             const int fz = kz <= d.nz ? kz : L - kz;
-            const R sz = kz > d.nz ? (R)-1 : (R)1;
-            const R sx = kx > d.nx ? (R)-1 : (R)1;
+            const unsigned mz = kz > d.nz ? SIGN_BIT : 0u;
+            const unsigned mx = kx > d.nx ? SIGN_BIT : 0u;
             const C* g = sG + fz * GS + lx;
-            C G[6];
-            G[0] = g[0];
-            G[1] = g[TX];
-            G[2] = g[2 * TX];
-            G[3] = cscale(g[3 * TX], sy * sz);
-            G[4] = cscale(g[4 * TX], sx * sz);
-            G[5] = cscale(g[5 * TX], sx * sy);
-            if (CONJ) {
-#pragma unroll
-                for (int c = 0; c < 6; ++c) G[c] = cconj(G[c]);
-            }
+            // mirrored octant entries: the off-diagonal ij entry is odd in axes i and j
+            const C G0 = g[0], G1 = g[TX], G2 = g[2 * TX];
+            const C G3 = flip_sign(g[3 * TX], my ^ mz);
+            const C G4 = flip_sign(g[4 * TX], mx ^ mz);
+            const C G5 = flip_sign(g[5 * TX], mx ^ my);
             C* row = s + kz * NL + lx;
             const C q0 = row[0], q1 = row[TX], q2 = row[2 * TX];
-            row[0] = cadd(cadd(cmul(G[0], q0), cmul(G[5], q1)), cmul(G[4], q2));
-            row[TX] = cadd(cadd(cmul(G[5], q0), cmul(G[1], q1)), cmul(G[3], q2));
-            row[2 * TX] = cadd(cadd(cmul(G[4], q0), cmul(G[3], q1)), cmul(G[2], q2));
+            row[0] = gdot3<CONJ>(G0, q0, G5, q1, G4, q2);
+            row[TX] = gdot3<CONJ>(G5, q0, G1, q1, G3, q2);
+            row[2 * TX] = gdot3<CONJ>(G4, q0, G3, q1, G2, q2);
         }
         __syncthreads();
         auto ld_s = [&](int l, int e) -> C { return s[e * NL + l]; };
@@ -542,7 +536,7 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_rows(const typen
         s[(i % L) * LD + i / L] = v[k];
     }
     __syncthreads();
-    fft4_smem<A, B, DIR>(s, NL, LD, tw, tid);
+    fft4_smem<A, B, DIR>(s, NL, LD, tw, tid, in_off + in_count);
     for (int i = tid; i < NL * out_count; i += NTHR) {
         const int e = i % out_count, l = i / out_count;
         const long long row = r0 + l;
@@ -1181,15 +1175,24 @@ cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* o
     return cudaGetLastError();
 }
 
+// Inside a stream capture the records become event-record nodes of the graph (external events),
+// so every replay records the same events again.
+static void ktimer_record(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
 void ktimer_mark(KTimer* t, int stage, bool f32, cudaStream_t st, int end) {
     if (!t || !t->on || !t->ev) return;
     if (!end) {
         if (t->used >= t->cap) return;
-        cudaEventRecord(t->ev[2 * t->used], st);
+        ktimer_record(t->ev[2 * t->used], st);
         t->tag[t->used] = (f32 ? 6 : 0) + stage;
         t->open = 1;
     } else if (t->open) {
-        cudaEventRecord(t->ev[2 * t->used + 1], st);
+        ktimer_record(t->ev[2 * t->used + 1], st);
         t->used++;
         t->open = 0;
     }

@@ -43,6 +43,27 @@ template <typename C> __device__ __forceinline__ C from_d2(double2 a);
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 
+// Sign flips by XOR of the IEEE sign bit (m = 0 or SIGN_BIT), on the integer pipe.
+constexpr unsigned SIGN_BIT = 0x80000000u;
+__device__ __forceinline__ float flip_sign(float v, unsigned m) { return __uint_as_float(__float_as_uint(v) ^ m); }
+__device__ __forceinline__ double flip_sign(double v, unsigned m) {
+    return __hiloint2double(__double2hiint(v) ^ (int)m, __double2loint(v));
+}
+__device__ __forceinline__ float2 flip_sign(float2 v, unsigned m) { return make_float2(flip_sign(v.x, m), flip_sign(v.y, m)); }
+__device__ __forceinline__ double2 flip_sign(double2 v, unsigned m) {
+    return make_double2(flip_sign(v.x, m), flip_sign(v.y, m));
+}
+
+// g0 qa + g1 qb + g2 qc (conj(g) for CONJ) as two chains of one multiply and five FMAs.
+template <bool CONJ, typename C>
+__device__ __forceinline__ C gdot3(C g0, C qa, C g1, C qb, C g2, C qc) {
+    typedef typename real_of<C>::type R;
+    const R s = CONJ ? (R)-1 : (R)1;
+    const R re = g0.x * qa.x - (s * g0.y) * qa.y + g1.x * qb.x - (s * g1.y) * qb.y + g2.x * qc.x - (s * g2.y) * qc.y;
+    const R im = g0.x * qa.y + (s * g0.y) * qa.x + g1.x * qb.y + (s * g1.y) * qb.x + g2.x * qc.y + (s * g2.y) * qc.x;
+    return mkc<C>(re, im);
+}
+
 // Asynchronous global -> shared copies (sm_80+ cp.async): 8- or 16-byte elements.
 template <typename C>
 __device__ __forceinline__ void cp_async_elem(C* smem_dst, const C* gmem_src) {

@@ -32,13 +32,26 @@ template <int S, typename C> __device__ __forceinline__ void bfly4(C* v) {
     v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
 }
 
-template <int S, typename C> __device__ __forceinline__ void bfly8(C* v) {
+// 4-point DFT of (v0, v1, 0, 0): the first radix-2 layer has nothing to add.
+template <int S, typename C> __device__ __forceinline__ void bfly4_half(C* v) {
+    const C a = v[0], b = v[1], bi = cmul_si<S>(v[1]);
+    v[0] = cadd(a, b); v[2] = csub(a, b);
+    v[1] = cadd(a, bi); v[3] = csub(a, bi);
+}
+
+// HALF: inputs 4..7 are zero (zero-padded lines), so each 4-point half-DFT has two zero inputs.
+template <int S, bool HALF = false, typename C> __device__ __forceinline__ void bfly8(C* v) {
     typedef typename real_of<C>::type T;
     const T r2 = (T)0.70710678118654752440;  // 1/sqrt(2)
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
-    bfly4<S>(e);
-    bfly4<S>(o);
+    if (HALF) {
+        bfly4_half<S>(e);
+        bfly4_half<S>(o);
+    } else {
+        bfly4<S>(e);
+        bfly4<S>(o);
+    }
     // twiddles w^s, w = exp(S 2 pi i / 8)
     C o1 = mkc<C>((o[1].x - (T)S * o[1].y) * r2, (o[1].y + (T)S * o[1].x) * r2);     // * (1 + S i)/sqrt2
     C o2 = cmul_si<S>(o[2]);                                                          // * S i

@@ -21,7 +21,8 @@ __device__ __forceinline__ C cmul_const(C a, double re, double im_s) {
 }
 
 // 16-point DFT in registers, natural order in and out: n = 4 n1 + n2, k = k1 + 4 k2.
-template <int S, typename C> __device__ __forceinline__ void bfly16(C* v) {
+// HALF: inputs 8..15 are zero, i.e. n1 = 2, 3 vanish in every first-layer 4-point DFT.
+template <int S, bool HALF = false, typename C> __device__ __forceinline__ void bfly16(C* v) {
     const double c1 = 0.92387953251128675613;  // cos(pi/8)
     const double s1 = 0.38268343236508977173;  // sin(pi/8)
     const double r2 = 0.70710678118654752440;  // 1/sqrt(2)
@@ -29,7 +30,8 @@ template <int S, typename C> __device__ __forceinline__ void bfly16(C* v) {
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) {
         C a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
-        bfly4<S>(a);
+        if (HALF) bfly4_half<S>(a);
+        else bfly4<S>(a);
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = a[k1];
     }
@@ -52,11 +54,19 @@ template <int S, typename C> __device__ __forceinline__ void bfly16(C* v) {
     }
 }
 
-template <int R, int S, typename C> __device__ __forceinline__ void dft_reg(C* v) {
-    if (R == 2) bfly2<S>(v);
-    else if (R == 4) bfly4<S>(v);
-    else if (R == 8) bfly8<S>(v);
-    else bfly16<S>(v);
+// R-point DFT in registers; HALF: inputs R/2 .. R-1 are zero.
+template <int R, int S, bool HALF = false, typename C> __device__ __forceinline__ void dft_reg(C* v) {
+    if (R == 2) {
+        if (HALF) v[1] = v[0];
+        else bfly2<S>(v);
+    } else if (R == 4) {
+        if (HALF) bfly4_half<S>(v);
+        else bfly4<S>(v);
+    } else if (R == 8) {
+        bfly8<S, HALF>(v);
+    } else {
+        bfly16<S, HALF>(v);
+    }
 }
 
 template <int A, int B> struct FourStep {
@@ -68,8 +78,10 @@ template <int A, int B> struct FourStep {
 
 // In-place FFT (sign S) of NL lines; called by exactly NL * TPL threads, tid < NL * TPL.
 // The caller synchronises before (input written) and gets the result after the final barrier.
+// Elements e >= nin are known to be zero (zero padding): a step-1 DFT whose upper half of
+// inputs lies there skips their loads and its first radix-2 layer.
 template <int A, int B, int S, typename C>
-__device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restrict__ tw, int tid) {
+__device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restrict__ tw, int tid, int nin = A * B) {
     typedef FourStep<A, B> F;
     const int l = tid % NL;
     const int q = tid / NL;
@@ -77,9 +89,15 @@ __device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restr
 #pragma unroll
     for (int i = 0; i < F::I1; ++i) {
         const int t = q + F::TPL * i;
+        if (t + B * (A / 2) >= nin) {
 #pragma unroll
-        for (int a = 0; a < A; ++a) v[i][a] = s[(t + B * a) * LD + l];
-        dft_reg<A, S>(v[i]);
+            for (int a = 0; a < A / 2; ++a) v[i][a] = s[(t + B * a) * LD + l];
+            dft_reg<A, S, true>(v[i]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < A; ++a) v[i][a] = s[(t + B * a) * LD + l];
+            dft_reg<A, S>(v[i]);
+        }
         if (t) {
 #pragma unroll
             for (int k1 = 1; k1 < A; ++k1) {
@@ -136,9 +154,11 @@ __host__ __device__ constexpr int fft4_ystride(int NL) {
 // (IN_SMEM: it reads the buffer s itself, so a barrier separates those reads from the first
 // write into s); st(l, k, v) receives output k of line l (OUT_SMEM: it writes s, so a barrier
 // separates the last reads of s from those writes).  Called by exactly NL * TPL threads.  The
-// intermediate occupies B * fft4_ystride<A, C>(NL) elements of s.
+// intermediate occupies B * fft4_ystride<A, C>(NL) elements of s.  Inputs e >= nin are known to
+// be zero: ld is not called for them, and a step-1 DFT whose upper half of inputs lies there
+// skips its first radix-2 layer.
 template <int A, int B, int S, bool IN_SMEM, bool OUT_SMEM, int NL, typename C, class Ld, class St>
-__device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid, Ld ld, St st) {
+__device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid, Ld ld, St st, int nin = A * B) {
     typedef FourStep<A, B> F;
     const int l = tid % NL;
     const int q = tid / NL;
@@ -147,13 +167,15 @@ __device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid,
 #pragma unroll
     for (int i = 0; i < F::I1; ++i) {
         const int t = q + F::TPL * i;
+        if (t + B * (A / 2) >= nin) {
 #pragma unroll
-        for (int a = 0; a < A; ++a) v[i][a] = ld(l, t + B * a);
-    }
+            for (int a = 0; a < A / 2; ++a) v[i][a] = ld(l, t + B * a);
+            dft_reg<A, S, true>(v[i]);
+        } else {
 #pragma unroll
-    for (int i = 0; i < F::I1; ++i) {
-        const int t = q + F::TPL * i;
-        dft_reg<A, S>(v[i]);
+            for (int a = 0; a < A; ++a) v[i][a] = ld(l, t + B * a);
+            dft_reg<A, S>(v[i]);
+        }
         if (t) {
 #pragma unroll
             for (int k1 = 1; k1 < A; ++k1) {

@@ -17,6 +17,8 @@
 
 namespace lsm {
 
+constexpr int MAXM = 8;   // moment tensors per source launch
+
 struct GreenPar {
     double a, b, rho, w;   // P, S velocities, density, angular frequency
     int mode;              // 0 exact, 1 paper
@@ -114,8 +116,15 @@ __global__ void k_green_table(Dims d, GreenPar p, double2 self, double2* __restr
 
 // u0_i = -sum_jk M_jk dG_ij/dx_k (x - s)
 //      = -[(f' + g/r) (M g)_i + (g' - 2 g/r)(g.M g) g_i + (g/r) tr(M) g_i]
-__global__ void k_source(Dims d, GreenPar p, double M11, double M22, double M33, double M23, double M13, double M12,
-                         double sx, double sy, double sz, double2* __restrict__ u0, int* __restrict__ flag) {
+// for up to MAXM moment tensors at one source position: the radial factors (the transcendental
+// part) are evaluated once per node and contracted with every tensor of the set.
+struct MomentSet {
+    int nm;
+    double M[MAXM][6];       // Voigt 11, 22, 33, 23, 13, 12
+    double2* u0[MAXM];
+};
+
+__global__ void k_source(Dims d, GreenPar p, MomentSet ms, double sx, double sy, double sz, int* __restrict__ flag) {
     const long long N = d.N;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int ix = (int)(i % d.nx);
@@ -124,25 +133,31 @@ __global__ void k_source(Dims d, GreenPar p, double M11, double M22, double M33,
         const double x = ix * d.h - sx, y = iy * d.h - sy, z = iz * d.h - sz;
         const double r = sqrt(x * x + y * y + z * z);
         if (r == 0.0) {
-            for (int c = 0; c < 3; ++c) u0[c * N + i] = make_double2(0.0, 0.0);
+            for (int m = 0; m < ms.nm; ++m)
+                for (int c = 0; c < 3; ++c) ms.u0[m][c * N + i] = make_double2(0.0, 0.0);
             atomicExch(flag, 1);
             continue;
         }
         const double g[3] = {x / r, y / r, z / r};
         double2 f, gg, fp, gp;
         radial(p, r, f, gg, fp, gp);
-        const double Mg[3] = {M11 * g[0] + M12 * g[1] + M13 * g[2],
-                              M12 * g[0] + M22 * g[1] + M23 * g[2],
-                              M13 * g[0] + M23 * g[1] + M33 * g[2]};
-        const double gMg = g[0] * Mg[0] + g[1] * Mg[1] + g[2] * Mg[2];
-        const double tr = M11 + M22 + M33;
         const double ir = 1.0 / r;
         const double2 A = make_double2(fp.x + gg.x * ir, fp.y + gg.y * ir);
         const double2 B = make_double2(gp.x - 2.0 * gg.x * ir, gp.y - 2.0 * gg.y * ir);
         const double2 Cc = make_double2(gg.x * ir, gg.y * ir);
-        for (int c = 0; c < 3; ++c) {
-            const double s1 = Mg[c], s2 = gMg * g[c], s3 = tr * g[c];
-            u0[c * N + i] = make_double2(-(A.x * s1 + B.x * s2 + Cc.x * s3), -(A.y * s1 + B.y * s2 + Cc.y * s3));
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) {
+            if (m >= ms.nm) break;
+            const double* M = ms.M[m];   // 11 22 33 23 13 12
+            const double Mg[3] = {M[0] * g[0] + M[5] * g[1] + M[4] * g[2],
+                                  M[5] * g[0] + M[1] * g[1] + M[3] * g[2],
+                                  M[4] * g[0] + M[3] * g[1] + M[2] * g[2]};
+            const double gMg = g[0] * Mg[0] + g[1] * Mg[1] + g[2] * Mg[2];
+            const double tr = M[0] + M[1] + M[2];
+            for (int c = 0; c < 3; ++c) {
+                const double s1 = Mg[c], s2 = gMg * g[c], s3 = tr * g[c];
+                ms.u0[m][c * N + i] = make_double2(-(A.x * s1 + B.x * s2 + Cc.x * s3), -(A.y * s1 + B.y * s2 + Cc.y * s3));
+            }
         }
     }
 }
@@ -244,17 +259,27 @@ cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, dou
     return launch_extract_octant(d, scratch, ghat64, 1.0 / (double)P, st, nl);
 }
 
-cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green, const double* M6,
-                          const double* xs, double2* u0, int* flag, cudaStream_t st, long long* nl) {
+cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green, int nm,
+                          const double* M6, const double* xs, double2* const* u0, int* flag, cudaStream_t st, long long* nl) {
     GreenPar p;
     p.a = sqrt((lam + 2.0 * mu) / rho);
     p.b = sqrt(mu / rho);
     p.rho = rho;
     p.w = omega;
     p.mode = green;
-    k_source<<<gsz(d.N), 256, 0, st>>>(d, p, M6[0], M6[1], M6[2], M6[3], M6[4], M6[5], xs[0], xs[1], xs[2], u0, flag);
-    if (nl) *nl += 1;
-    return cudaGetLastError();
+    for (int m0 = 0; m0 < nm; m0 += MAXM) {
+        MomentSet ms;
+        ms.nm = nm - m0 < MAXM ? nm - m0 : MAXM;
+        for (int m = 0; m < ms.nm; ++m) {
+            for (int k = 0; k < 6; ++k) ms.M[m][k] = M6[6 * (m0 + m) + k];
+            ms.u0[m] = u0[m0 + m];
+        }
+        k_source<<<gsz(d.N), 256, 0, st>>>(d, p, ms, xs[0], xs[1], xs[2], flag);
+        if (nl) *nl += 1;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_source_gradient(const Dims& d, double lam, double mu, double rho, double omega, int green,

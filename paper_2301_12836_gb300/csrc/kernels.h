@@ -77,9 +77,10 @@ cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, dou
                                double omega, int green, double2* scratch, double2* ghat64,
                                cudaStream_t st, long long* nlaunch);
 
-// Background field u0 of a moment tensor (complex double), flag set to 1 if a node hits the source.
-cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green,
-                          const double* M6, const double* xs, double2* u0, int* flag,
+// Background fields u0[m] of nm moment tensors M6[6m..6m+5] at one position (complex double);
+// flag set to 1 if a node hits the source.
+cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green, int nm,
+                          const double* M6, const double* xs, double2* const* u0, int* flag,
                           cudaStream_t st, long long* nlaunch);
 
 // Absorbing-boundary weight (Eq. 25) applied in place to the 21 contrast planes and drho (FP64).

@@ -44,7 +44,23 @@ struct SolverWS {
     std::vector<void*> kry;    // KRY Krylov vectors per system (inner precision)
     std::vector<void*> w1, w2; // inner-precision apply workspaces
     std::vector<double2*> w1d, w2d, ax64;
+    // captured BiCGSTAB iterations, one per (precision, direction); valid while block is
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int nsys = 0;
+        int timer_on = 0;
+        long long launches = 0;   // kernels per replay
+        std::vector<int> tags;    // timer slots of the captured event pairs
+    } graph[2][2];                // [FP32][adjoint]
 };
+
+void drop_graphs(SolverWS& w) {
+    for (auto& row : w.graph)
+        for (auto& g : row) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = SolverWS::Graph();
+        }
+}
 
 struct Store {
     int refs = 1;
@@ -71,6 +87,7 @@ struct Store {
     double* grad_scratch = nullptr;        // moment-gradient partial sums
     KTimer timer;
     SolverWS ws;
+    cudaStream_t cap_st = nullptr;         // private stream the iteration graphs are captured on
 };
 
 }  // namespace
@@ -148,7 +165,9 @@ void store_release(Store* s) {
         delete[] s->timer.tag;
     }
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    drop_graphs(s->ws);
     cudaFree(s->ws.block);
+    if (s->cap_st) cudaStreamDestroy(s->cap_st);
     delete s;
 }
 
@@ -187,6 +206,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->inner_tol = 1e-6;
     o->max_outer = 8;
     o->taper = 0;
+    o->graph = 1;
 }
 
 static lsm_status build_spectrum(lsm_t h) {
@@ -223,7 +243,8 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     lsm_default_opts(&o);
     if (opts) o = *opts;
     if ((o.precision != LSM_FP64 && o.precision != LSM_MIXED) || (o.green != LSM_GREEN_EXACT && o.green != LSM_GREEN_PAPER) ||
-        !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1 || o.taper < 0)
+        !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1 || o.taper < 0 ||
+        (o.graph != 0 && o.graph != 1))
         return fail(nullptr, LSM_ERR_ARG, "lsm_create: invalid options");
     static bool attrs_done = false;
     if (!attrs_done) {
@@ -330,23 +351,37 @@ extern "C" const char* lsm_last_error(lsm_t h) {
 
 extern "C" long long lsm_launch_count(lsm_t h) { return h ? h->nl : 0; }
 
-extern "C" lsm_status lsm_source(lsm_t h, const double M[6], const double xs[3], void* u0) {
-    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_source: null handle");
-    if (!M || !xs || !u0) return fail(h, LSM_ERR_ARG, "lsm_source: null pointer argument");
-    for (int k = 0; k < 6; ++k)
-        if (!std::isfinite(M[k])) return fail(h, LSM_ERR_ARG, "lsm_source: moment tensor not finite");
+static lsm_status source_fields(lsm_t h, const char* who, int nm, const double* M, const double* xs, void* const* u0) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, std::string(who) + ": null handle");
+    if (!M || !xs || !u0) return fail(h, LSM_ERR_ARG, std::string(who) + ": null pointer argument");
+    if (nm < 1 || nm > 4096) return fail(h, LSM_ERR_ARG, std::string(who) + ": nm must be in 1..4096");
+    for (int m = 0; m < nm; ++m) {
+        if (!u0[m]) return fail(h, LSM_ERR_ARG, std::string(who) + ": null output pointer");
+        for (int k = 0; k < 6; ++k)
+            if (!std::isfinite(M[6 * m + k])) return fail(h, LSM_ERR_ARG, std::string(who) + ": moment tensor not finite");
+    }
     for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(xs[k])) return fail(h, LSM_ERR_ARG, "lsm_source: source position not finite");
+        if (!std::isfinite(xs[k])) return fail(h, LSM_ERR_ARG, std::string(who) + ": source position not finite");
     Store* s = h->s;
     CK(h, cudaMemsetAsync(s->flag, 0, sizeof(int), s->st));
-    CK(h, launch_source(s->d, s->lam, s->mu, s->rho, h->omega, s->green, M, xs, (double2*)u0, s->flag, s->st, &h->nl));
+    CK(h, launch_source(s->d, s->lam, s->mu, s->rho, h->omega, s->green, nm, M, xs, (double2* const*)u0, s->flag, s->st,
+                        &h->nl));
     CK(h, cudaMemcpyAsync(s->h_pinned, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->st));
     CK(h, cudaStreamSynchronize(s->st));
     if (s->h_pinned[0]) {
-        h->err = "lsm_source: a grid node coincides with the source; u0 set to 0 there";
+        h->err = std::string(who) + ": a grid node coincides with the source; u0 set to 0 there";
         return LSM_WARN_SOURCE_ON_NODE;
     }
     return LSM_OK;
+}
+
+extern "C" lsm_status lsm_source(lsm_t h, const double M[6], const double xs[3], void* u0) {
+    void* out[1] = {u0};
+    return source_fields(h, "lsm_source", 1, M, xs, out);
+}
+
+extern "C" lsm_status lsm_source_moments(lsm_t h, int nm, const double* M, const double xs[3], void* const* u0) {
+    return source_fields(h, "lsm_source_moments", nm, M, xs, u0);
 }
 
 template <typename T>
@@ -400,11 +435,14 @@ namespace {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr int GRAPH_ITERS = 2;   // BiCGSTAB iterations per captured graph
+
 lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     Store* s = h->s;
     SolverWS& w = s->ws;
     const long long n3 = 3 * s->d.N;
     if (w.cap >= nsys && w.precision == s->precision) return LSM_OK;
+    drop_graphs(w);
     cudaFree(w.block);
     w = SolverWS();
     long long e1, e2;
@@ -519,20 +557,72 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
     CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(h0, cudaStreamSynchronize(st));
     int n_active = s->h_pinned[0];
-    int guard = 0;
-    while (n_active > 0 && guard++ <= maxit + 1) {
-        CK(h0, bcg_update_p<T>(vecs, w.st, n3, nsys, pt.nblk, st, nl));
-        cudaError_t e = apply_op<T>(adjoint, m, pl, sv, nsys, st, nl);
-        if (e != cudaSuccess) return cuda_fail(h0, e, "apply p");
-        CK(h0, bcg_alpha<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
-        CK(h0, bcg_s<T>(vecs, w.st, pt, n3, nsys, st, nl));
-        e = apply_op<T>(adjoint, m, pl, stt, nsys, st, nl);
-        if (e != cudaSuccess) return cuda_fail(h0, e, "apply s");
-        CK(h0, bcg_omega<T>(vecs, w.st, pt, n3, nsys, st, nl));
-        CK(h0, bcg_xr<T>(vecs, w.st, pt, n3, nsys, w.n_active, st, nl));
+    // one iteration for every system on stream q; kernels of systems that stopped return at once
+    auto iterate = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = bcg_update_p<T>(vecs, w.st, n3, nsys, pt.nblk, q, nl);
+        if (e == cudaSuccess) e = apply_op<T>(adjoint, m, pl, sv, nsys, q, nl);
+        if (e == cudaSuccess) e = bcg_alpha<T>(vecs, w.st, pt, n3, nsys, w.n_active, q, nl);
+        if (e == cudaSuccess) e = bcg_s<T>(vecs, w.st, pt, n3, nsys, q, nl);
+        if (e == cudaSuccess) e = apply_op<T>(adjoint, m, pl, stt, nsys, q, nl);
+        if (e == cudaSuccess) e = bcg_omega<T>(vecs, w.st, pt, n3, nsys, q, nl);
+        if (e == cudaSuccess) e = bcg_xr<T>(vecs, w.st, pt, n3, nsys, w.n_active, q, nl);
+        return e;
+    };
+    const bool use_graph = h0->o.graph != 0;
+    SolverWS::Graph& G = w.graph[f32 ? 1 : 0][adjoint ? 1 : 0];
+    KTimer& tm = s->timer;
+    int done = 0;   // iterations issued (each system also counts its own and stops at maxit)
+    while (n_active > 0 && done <= maxit + 1) {
+        if (!use_graph || done == 0) {
+            // eager: always the first iteration, so every kernel is loaded and configured
+            // before a capture
+            cudaError_t e = iterate(st);
+            if (e != cudaSuccess) return cuda_fail(h0, e, "BiCGSTAB iteration");
+            done += 1;
+        } else {
+            const int tm_on = (tm.on && tm.ev) ? 1 : 0;
+            if (G.exec && (G.nsys != nsys || G.timer_on != tm_on)) {
+                cudaGraphExecDestroy(G.exec);
+                G = SolverWS::Graph();
+            }
+            if (!G.exec) {
+                // captured on a private stream (the caller's may be the legacy default stream,
+                // which cannot be captured); replayed on the caller's
+                if (!s->cap_st) CK(h0, cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+                const long long nl0 = *nl;
+                tm.used = 0;
+                tm.open = 0;
+                CK(h0, cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = cudaSuccess;
+                for (int k = 0; k < GRAPH_ITERS && e == cudaSuccess; ++k) e = iterate(s->cap_st);
+                cudaGraph_t g = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(s->cap_st, &g);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+                if (g) cudaGraphDestroy(g);
+                *nl = nl0;
+                if (e != cudaSuccess) {
+                    G = SolverWS::Graph();
+                    tm.used = 0;
+                    return cuda_fail(h0, e, "BiCGSTAB iteration graph");
+                }
+                G.nsys = nsys;
+                G.timer_on = tm_on;
+                G.launches = *nl - nl0;
+                G.tags.assign(tm.tag, tm.tag + tm.used);
+                tm.used = 0;
+            }
+            CK(h0, cudaGraphLaunch(G.exec, st));
+            *nl += G.launches;
+            if (tm_on) {
+                std::copy(G.tags.begin(), G.tags.end(), tm.tag);
+                tm.used = (int)G.tags.size();
+            }
+            done += GRAPH_ITERS;
+        }
         CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(h0, cudaStreamSynchronize(st));
-        ktimer_flush(&s->timer);
+        ktimer_flush(&tm);
         n_active = s->h_pinned[0];
     }
     out.resize(nsys);

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
                 -5: "LSM_ERR_NOCONV", -6: "LSM_ERR_TIMEOUT", 1: "LSM_WARN_SOURCE_ON_NODE"}
 
 # every symbol the header declares, in declaration order
-EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_apply", "lsm_apply_c64",
+EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_source_moments", "lsm_apply", "lsm_apply_c64",
            "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
            "lsm_source_gradient", "lsm_time_traces", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
@@ -40,7 +40,7 @@ EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", 
 
 class lsm_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("green", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
-                ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int)]
+                ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int), ("graph", ct.c_int)]
 
 
 class LSMError(RuntimeError):
@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH):
     lib.lsm_create_shared.restype = i
     lib.lsm_source.argtypes = [vp, ct.POINTER(d), ct.POINTER(d), vp]
     lib.lsm_source.restype = i
+    lib.lsm_source_moments.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(d), ct.POINTER(vp)]
+    lib.lsm_source_moments.restype = i
     for name in ("lsm_apply", "lsm_apply_c64", "lsm_adjoint"):
         getattr(lib, name).argtypes = [vp, vp, vp]
         getattr(lib, name).restype = i
@@ -177,6 +179,18 @@ def lsm_source(h: Handle, M6, xs, u0: torch.Tensor) -> int:
     x = (ct.c_double * 3)(*[float(v) for v in xs])
     return _check(load().lsm_source(h.ptr, M, x, _ptr(u0, torch.complex128, 3 * h.N)), h.ptr,
                   allow=(LSM_WARN_SOURCE_ON_NODE,))
+
+
+def lsm_source_moments(h: Handle, Ms, xs, u0s) -> int:
+    """Background fields of several moment tensors (rows of Ms, Voigt order) at one position."""
+    Ms = [[float(v) for v in m] for m in Ms]
+    nm = len(Ms)
+    if len(u0s) != nm:
+        raise ValueError("lsm_source_moments: one output per moment tensor")
+    M = (ct.c_double * (6 * nm))(*[v for m in Ms for v in m])
+    x = (ct.c_double * 3)(*[float(v) for v in xs])
+    outs = (ct.c_void_p * nm)(*[_ptr(u, torch.complex128, 3 * h.N) for u in u0s])
+    return _check(load().lsm_source_moments(h.ptr, nm, M, x, outs), h.ptr, allow=(LSM_WARN_SOURCE_ON_NODE,))
 
 
 def lsm_apply(h: Handle, u: torch.Tensor, Au: torch.Tensor) -> None:

@@ -41,6 +41,38 @@ def test_source_parity(mode, green):
     assert rel(host(u0).reshape(want.shape), want) < 1e-12
 
 
+@pytest.mark.parametrize("mode,green", [("exact", lsm.LSM_GREEN_EXACT), ("paper", lsm.LSM_GREEN_PAPER)])
+def test_source_moments_parity(mode, green):
+    """Ten moment tensors at one position (two launches of up to eight): each field matches the
+    oracle and is bitwise the field lsm_source gives for that tensor alone."""
+    med = sy.random_medium((12, 10, 9), h=10.0, seed=23)
+    h = handle(med, W, green=green)
+    xs = np.array([53.1, 41.7, 38.4])
+    Ms = sy.random_moment_tensors(10, np.random.default_rng(24))
+    outs = [torch.empty(3 * h.N, dtype=torch.complex128, device="cuda") for _ in Ms]
+    assert lsm.lsm_source_moments(h, Ms, xs, outs) == lsm.LSM_OK
+    for M, u0 in zip(Ms, outs):
+        want, _ = osrc.background_field(med.n, med.h, M, xs, W, med.lam0, med.mu0, med.rho0, mode)
+        assert rel(host(u0).reshape(want.shape), want) < 1e-12
+        one = torch.empty_like(u0)
+        lsm.lsm_source(h, M, xs, one)
+        assert torch.equal(one, u0)
+
+
+def test_source_moments_on_node_and_bad_arguments():
+    med = sy.random_medium((6, 6, 6), h=10.0, seed=22)
+    h = handle(med, W)
+    outs = [torch.empty(3 * h.N, dtype=torch.complex128, device="cuda") for _ in range(2)]
+    Ms = [sy.explosion(), sy.double_couple_12()]
+    assert lsm.lsm_source_moments(h, Ms, [20.0, 30.0, 40.0], outs) == lsm.LSM_WARN_SOURCE_ON_NODE
+    for u0 in outs:
+        assert np.all(host(u0).reshape(3, 6, 6, 6)[:, 4, 3, 2] == 0)
+    with pytest.raises(lsm.LSMError):
+        lsm.lsm_source_moments(h, [[np.nan] * 6], [1.0, 2.0, 3.0], outs[:1])
+    with pytest.raises(lsm.LSMError):
+        lsm.lsm_source_moments(h, [], [1.0, 2.0, 3.0], [])
+
+
 def test_source_on_node_flag():
     med = sy.random_medium((6, 6, 6), h=10.0, seed=22)
     h = handle(med, W)
@@ -179,6 +211,38 @@ def test_solve_batched_frequencies_and_sources(precision, tol, bar):
     for x, xo, rr in zip(xs, want, rrs):
         assert rr <= tol
         assert rel(host(x).reshape(xo.shape), xo) < bar
+
+
+@pytest.mark.parametrize("precision,tol", [(lsm.LSM_FP64, 1e-11), (lsm.LSM_MIXED, 1e-8)])
+def test_graph_replay_matches_eager_launches(precision, tol):
+    """The BiCGSTAB iterations replayed from a captured CUDA graph give bitwise the iterates of
+    host-launched kernels (same kernels, same order, deterministic reductions); the graph is
+    reused by a second solve, and the stage timer still sees every apply."""
+    med = sy.random_medium((12, 10, 9), h=10.0, seed=31, frac=0.1)
+    srcs = [(sy.explosion(), np.array([44.0, 41.0, 37.0])), (sy.double_couple_12(), np.array([31.0, 52.0, 45.0])),
+            (sy.double_couple_13(), np.array([61.0, 22.0, 45.0]))]
+    out = {}
+    for graph in (0, 1):
+        h = handle(med, 2 * np.pi * 9.0, precision=precision, tol=tol, graph=graph)
+        bs = []
+        for M, s in srcs:
+            b = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+            lsm.lsm_source(h, M, s, b)
+            bs.append(b)
+        runs = []
+        for rep in range(2):
+            lsm.lsm_timer_start(h, True)
+            xs = [torch.zeros_like(b) for b in bs]
+            code, its, rrs, sts = lsm.lsm_solve_batched([h] * len(bs), bs, xs)
+            assert code == lsm.LSM_OK and all(r <= tol for r in rrs)
+            ms, launches, applies = lsm.lsm_timer_read(h)
+            runs.append((torch.stack(xs).cpu(), its, rrs, applies))
+            assert sum(launches) > 0 and sum(ms) > 0
+        assert torch.equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
+        out[graph] = runs[0]
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert tuple(out[0][3]) == tuple(out[1][3])   # executed system applies per precision
 
 
 def test_solve_zero_rhs_and_noconv():
