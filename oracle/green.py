@@ -150,3 +150,30 @@ def kernel_table(n, h, omega, lam, mu, rho, mode="exact"):
     G = np.moveaxis(G, (-2, -1), (0, 1))              # (3, 3, z, y, x)
     T[:, :, MZ % (2 * nz), MY % (2 * ny), MX % (2 * nx)] = G
     return T
+
+
+def h_table(n, h, omega, lam, mu, rho, mode="exact"):
+    """Sampled derivative kernel of Eqs. 9-10 on the 2n-periodic grid, shape (3, 6, 2nz, 2ny, 2nx).
+
+    Entry [i, J, m] is the weight of the Voigt stress sigma_J in u_s,i = sum_jk (dG_ij/dx_k) * sigma_jk
+    (Eq. 8 after partial integration): h^3 dG_ij/dx_k (m h) for J = (j, j), and
+    h^3 (dG_ij/dx_k + dG_ik/dx_j)(m h) for J = (j, k), j != k (both orderings of the symmetric
+    stress).  Zero at m = 0 (the cell average of an odd function) and on the planes m_a = n_a;
+    index layout as in ``kernel_table``.
+    """
+    nx, ny, nz = n
+    T = np.zeros((3, 6, 2 * nz, 2 * ny, 2 * nx), dtype=np.complex128)
+    mx = np.arange(-(nx - 1), nx)
+    my = np.arange(-(ny - 1), ny)
+    mz = np.arange(-(nz - 1), nz)
+    MZ, MY, MX = np.meshgrid(mz, my, mx, indexing="ij")
+    off = np.stack([MX, MY, MZ], axis=-1).astype(np.float64) * h
+    zero = (MX == 0) & (MY == 0) & (MZ == 0)
+    off[zero] = 1.0  # placeholder, zeroed below
+    dG = dgreen(off, omega, lam, mu, rho, mode) * h ** 3            # (z, y, x, i, j, k)
+    dG[zero] = 0.0
+    voigt = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+    for J, (j, k) in enumerate(voigt):
+        w = dG[..., :, j, k] if j == k else dG[..., :, j, k] + dG[..., :, k, j]
+        T[:, J][:, MZ % (2 * nz), MY % (2 * ny), MX % (2 * nx)] = np.moveaxis(w, -1, 0)
+    return T

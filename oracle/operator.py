@@ -21,6 +21,11 @@ Definitions (Sec. 2-3; readings listed where the paper is silent):
 ``apply_fft`` evaluates the same operator in the form of Eq. 21: FFTs on the
 2n-periodic grid, the spectrum of T, and the derivative D_k applied as the
 factor i kappa_k with kappa_k = sin(k_k h) / h.
+
+Sampled-H form (Eq. 21 with H taken literally): the derivative of Eq. 9 is not a difference
+but the analytic dG of Appendix A sampled on the grid (``green.h_table``):
+u_s,i(x) = sum_x' [sum_J H_iJ(x - x') sigma_J(x') + w^2 sum_j T_ij(x - x') drho u_j(x')] over
+the model's nodes x'; ``apply_direct_h`` sums this directly, ``FFTOperator(form="h")`` by FFT.
 """
 from __future__ import annotations
 
@@ -131,6 +136,34 @@ def apply_direct(u, medium, omega, mode="exact"):
     return u - scatter_direct(q, T, medium.n)
 
 
+def scatter_direct_h(sig, w, htab, table, n):
+    """Sampled-H scattered field by brute-force summation over the model's nodes (small n only):
+    u_s,i(x) = sum_x' sum_J H_iJ(x - x') sig_J(x') + sum_j T_ij(x - x') w_j(x')."""
+    nx, ny, nz = n
+    us = np.zeros((3, nz, ny, nx), dtype=np.complex128)
+    src = [np.arange(m) for m in (nz, ny, nx)]
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                mz = (z - src[0]) % (2 * nz)
+                my = (y - src[1]) % (2 * ny)
+                mx = (x - src[2]) % (2 * nx)
+                sel = (mz[:, None, None], my[None, :, None], mx[None, None, :])
+                Hloc = htab[:, :, sel[0], sel[1], sel[2]]
+                Tloc = table[:, :, sel[0], sel[1], sel[2]]
+                us[:, z, y, x] = np.einsum("iJabc,Jabc->i", Hloc, sig) + np.einsum("ijabc,jabc->i", Tloc, w)
+    return us
+
+
+def apply_direct_h(u, medium, omega, mode="exact"):
+    """A u of the sampled-H form by direct summation (no FFT), for small grids."""
+    args = (medium.n, medium.h, omega, medium.lam0, medium.mu0, medium.rho0, mode)
+    H = _green.h_table(*args)
+    T = _green.kernel_table(*args)
+    sig = stress(medium.dC, strain(u, medium.h))
+    return u - scatter_direct_h(sig, omega ** 2 * medium.drho * u, H, T, medium.n)
+
+
 class FFTOperator:
     """A u evaluated as in Eq. 21 on the 2n-periodic grid.
 
@@ -139,14 +172,20 @@ class FFTOperator:
     u_s = crop IFFT(T-hat q-hat), A u = u - u_s.
     """
 
-    def __init__(self, medium, omega, mode="exact"):
+    def __init__(self, medium, omega, mode="exact", form="fd"):
+        if form not in ("fd", "h"):
+            raise ValueError(form)
         self.m = medium
         self.omega = float(omega)
         self.n = medium.n
+        self.form = form
         nx, ny, nz = medium.n
         self.P = (2 * nz, 2 * ny, 2 * nx)
         T = _green.kernel_table(medium.n, medium.h, omega, medium.lam0, medium.mu0, medium.rho0, mode)
         self.That = np.fft.fftn(T, axes=(-3, -2, -1))
+        if form == "h":
+            H = _green.h_table(medium.n, medium.h, omega, medium.lam0, medium.mu0, medium.rho0, mode)
+            self.Hhat = np.fft.fftn(H, axes=(-3, -2, -1))
         h = medium.h
         kap = []
         for a, L in enumerate((2 * nx, 2 * ny, 2 * nz)):
@@ -170,6 +209,11 @@ class FFTOperator:
         sig = stress(m.dC, strain(u, m.h))
         sh = np.fft.fftn(self._pad(sig), axes=(-3, -2, -1))
         wh = np.fft.fftn(self._pad(m.drho * u), axes=(-3, -2, -1))
+        if self.form == "h":
+            # Eq. 21: u-hat_i = sum_J H-hat_iJ sigma-hat_J + w^2 sum_j T-hat_ij w-hat_j
+            uh = (np.einsum("iJ...,J...->i...", self.Hhat, sh)
+                  + self.omega ** 2 * np.einsum("ij...,j...->i...", self.That, wh))
+            return self._crop(np.fft.ifftn(uh, axes=(-3, -2, -1)))
         qh = self.omega ** 2 * wh
         for j in range(3):
             for k in range(3):
@@ -188,6 +232,8 @@ class FFTOperator:
         becomes its conjugate -i kappa; the stress and strain maps become the
         transposes of the (real) contrast matrix and strain operator.
         """
+        if self.form != "fd":
+            raise NotImplementedError("adjoint of the sampled-H form")
         m = self.m
         wh = np.fft.fftn(self._pad(w), axes=(-3, -2, -1))
         zh = np.einsum("ij...,i...->j...", np.conj(self.That), wh)
