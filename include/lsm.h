@@ -58,6 +58,7 @@ typedef enum {
 
 enum { LSM_FP64 = 0, LSM_MIXED = 1 };
 enum { LSM_GREEN_EXACT = 0, LSM_GREEN_PAPER = 1 };
+enum { LSM_KERNEL_DIFF = 0, LSM_KERNEL_H = 1 };
 
 typedef struct {
     int precision;     /* LSM_FP64: complex128 throughout.
@@ -80,6 +81,15 @@ typedef struct {
                           return at once) and replayed, one host synchronisation per replay;
                           the graph is kept with the solver workspace and reused by later solves
                           of the same batch size.  0: every kernel is launched from the host. */
+    int kernel;        /* LSM_KERNEL_DIFF (default): the derivative in H of Eq. 9 is taken as the
+                          central difference (Eq. 18's stencil) of the contrast stress, so three
+                          source components are transformed each way against 6 spectra.
+                          LSM_KERNEL_H: Eq. 21 literally, with H_iJ sampled from the analytic
+                          derivative of the Green's tensor (Appendix A, Eqs. A.6-A.11 for
+                          LSM_GREEN_PAPER) and transformed: 9 forward transforms (6 stress, 3
+                          density), 24 spectra (18 H, 6 G), about 4x the spectrum memory.  The
+                          adjoint calls (lsm_adjoint, lsm_solve_adjoint, lsm_gradient) and
+                          lsm_apply_static return LSM_ERR_ARG for it. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */

@@ -114,6 +114,51 @@ __global__ void k_green_table(Dims d, GreenPar p, double2 self, double2* __restr
     }
 }
 
+// Row i of the sampled derivative kernel of Eqs. 9-10 on the 2n-periodic grid, [6][Lz][Ly][Lx]:
+// entry J = (j, k) holds h^3 dG_ij/dx_k (m h) for j = k and h^3 (dG_ij/dx_k + dG_ik/dx_j)(m h) for
+// j != k (the weight of the Voigt stress sigma_J in u_s,i = sum_jk dG_ij/dx_k * sigma_jk); zero at
+// m = 0 (an odd kernel averages to zero over the cell) and on the planes m_a = n_a.
+__global__ void k_h_table(Dims d, GreenPar p, int i, double2* __restrict__ T) {
+    const long long P = (long long)d.Lx * d.Ly * d.Lz;
+    const double h3 = d.h * d.h * d.h;
+    const int vj[6] = {0, 1, 2, 1, 0, 0}, vk[6] = {0, 1, 2, 2, 2, 1};
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < P; idx += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(idx % d.Lx);
+        const int iy = (int)((idx / d.Lx) % d.Ly);
+        const int iz = (int)(idx / ((long long)d.Lx * d.Ly));
+        double2 out[6];
+        for (int c = 0; c < 6; ++c) out[c] = make_double2(0.0, 0.0);
+        const int mx = ix < d.nx ? ix : ix - d.Lx;
+        const int my = iy < d.ny ? iy : iy - d.Ly;
+        const int mz = iz < d.nz ? iz : iz - d.Lz;
+        if (ix != d.nx && iy != d.ny && iz != d.nz && (mx != 0 || my != 0 || mz != 0)) {
+            const double x[3] = {mx * d.h, my * d.h, mz * d.h};
+            const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            const double c[3] = {x[0] / r, x[1] / r, x[2] / r};
+            double2 f, g, fp, gp;
+            radial(p, r, f, g, fp, gp);
+            const double ir = 1.0 / r;
+            // dG_ij/dx_k = f' c_k d_ij + g' c_i c_j c_k + (g / r)(d_ik c_j + d_jk c_i - 2 c_i c_j c_k)
+            auto dG = [&](int a, int b, int k) -> double2 {
+                const double dab = a == b ? 1.0 : 0.0, dak = a == k ? 1.0 : 0.0, dbk = b == k ? 1.0 : 0.0;
+                const double t1 = c[k] * dab, t2 = c[a] * c[b] * c[k];
+                const double t3 = (dak * c[b] + dbk * c[a] - 2.0 * t2) * ir;
+                return make_double2(fp.x * t1 + gp.x * t2 + g.x * t3, fp.y * t1 + gp.y * t2 + g.y * t3);
+            };
+            for (int J = 0; J < 6; ++J) {
+                double2 v = dG(i, vj[J], vk[J]);
+                if (vj[J] != vk[J]) {
+                    const double2 w = dG(i, vk[J], vj[J]);
+                    v.x += w.x;
+                    v.y += w.y;
+                }
+                out[J] = make_double2(h3 * v.x, h3 * v.y);
+            }
+        }
+        for (int J = 0; J < 6; ++J) T[J * P + idx] = out[J];
+    }
+}
+
 // u0_i = -sum_jk M_jk dG_ij/dx_k (x - s)
 //      = -[(f' + g/r) (M g)_i + (g' - 2 g/r)(g.M g) g_i + (g/r) tr(M) g_i]
 // for up to MAXM moment tensors at one source position: the radial factors (the transcendental
@@ -233,7 +278,7 @@ cudaError_t fft3_inplace_setup(const Dims& d, const Plans& pl, double2* buf, int
 cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* oct, double scale, cudaStream_t st, long long* nl);
 
 cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, double mu, double rho, double omega,
-                               int green, double2* scratch, double2* ghat64, cudaStream_t st, long long* nl) {
+                               int green, int kernel, double2* scratch, double2* ghat64, cudaStream_t st, long long* nl) {
     GreenPar p;
     p.a = sqrt((lam + 2.0 * mu) / rho);
     p.b = sqrt(mu / rho);
@@ -256,7 +301,19 @@ cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, dou
     if (e != cudaSuccess) return e;
     e = fft3_inplace_setup(d, pl64, scratch, 6, st, nl);
     if (e != cudaSuccess) return e;
-    return launch_extract_octant(d, scratch, ghat64, 1.0 / (double)P, st, nl);
+    e = launch_extract_octant(d, scratch, ghat64, 1.0 / (double)P, st, nl);
+    if (e != cudaSuccess || kernel != 1) return e;
+    // sampled-H form: the three rows of H_iJ, six planes each, through the same scratch
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    for (int i = 0; i < 3; ++i) {
+        k_h_table<<<gsz(P), 256, 0, st>>>(d, p, i, scratch);
+        if (nl) *nl += 1;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = fft3_inplace_setup(d, pl64, scratch, 6, st, nl);
+        if (e == cudaSuccess) e = launch_extract_octant(d, scratch, ghat64 + (6 + 6 * i) * NO, 1.0 / (double)P, st, nl);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green, int nm,

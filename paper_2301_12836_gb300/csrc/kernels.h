@@ -12,7 +12,8 @@ struct ApplySys {
     typedef typename cplx_of<T>::type C;
     const C* u;          // input field [3][nz][ny][nx]
     C* out;              // result [3][nz][ny][nx]
-    const C* ghat;       // octant Green spectrum [6][nz+1][ny+1][nx+1], scaled by 1/P
+    const C* ghat;       // octant spectra [6 or 24][nz+1][ny+1][nx+1], scaled by 1/P: G (11 22 33 23 13 12),
+                         // then, in the sampled-H form, H_iJ at plane 6 + 6 i + J
     C* w1;               // workspace (see apply_ws_elems)
     C* w2;               // workspace
     T omega2;            // w^2
@@ -40,6 +41,7 @@ struct Medium {
     const void* dC;      // [21][N] of T
     const void* drho;    // [N] of T
     KTimer* timer;       // optional stage timer
+    int kernel;          // 0: difference form (6 spectra); 1: sampled-H form (24 spectra)
 };
 
 struct Plans {
@@ -49,8 +51,8 @@ struct Plans {
     const void* twz;
 };
 
-// workspace elements (complex) needed by one system's apply / adjoint, each of w1 and w2
-void apply_ws_elems(const Dims& d, long long* w1, long long* w2);
+// workspace elements (complex) needed by one system's apply / adjoint in w1 and w2 (kernel as in Medium)
+void apply_ws_elems(const Dims& d, int kernel, long long* w1, long long* w2);
 
 // Operator A u (forward) or A^H u (adjoint) for nsys systems; sys is a device array.
 template <typename T>
@@ -72,9 +74,10 @@ cudaError_t launch_source_gradient(const Dims& d, double lam, double mu, double 
                                    long long* nl);
 
 // Green spectrum setup: writes the octant spectrum (double) scaled by 1/P into ghat64,
-// using scratch (6 * Lx*Ly*Lz complex double).  green: 0 exact, 1 paper.
+// using scratch (6 * Lx*Ly*Lz complex double).  green: 0 exact, 1 paper.  kernel 1 (sampled-H form)
+// also writes the 18 octant spectra of H_iJ after the 6 of G (ghat64 then holds 24 planes).
 cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, double mu, double rho,
-                               double omega, int green, double2* scratch, double2* ghat64,
+                               double omega, int green, int kernel, double2* scratch, double2* ghat64,
                                cudaStream_t st, long long* nlaunch);
 
 // Background fields u0[m] of nm moment tensors M6[6m..6m+5] at one position (complex double);

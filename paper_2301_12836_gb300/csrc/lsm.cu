@@ -68,6 +68,7 @@ struct Store {
     double lam = 0, mu = 0, rho = 0;
     int precision = LSM_FP64, green = LSM_GREEN_EXACT;
     int taper = 0;
+    int kernel = LSM_KERNEL_DIFF;
     cudaStream_t st = nullptr;
     double* dC64 = nullptr;
     double* drho64 = nullptr;
@@ -174,7 +175,7 @@ void store_release(Store* s) {
 lsm_status ensure_apply_ws(lsm_t h) {
     Store* s = h->s;
     long long e1, e2;
-    apply_ws_elems(s->d, &e1, &e2);
+    apply_ws_elems(s->d, s->kernel, &e1, &e2);
     if (!s->w1_64) {
         CK(h, cudaMalloc(&s->w1_64, e1 * sizeof(double2)));
         CK(h, cudaMalloc(&s->w2_64, e2 * sizeof(double2)));
@@ -192,6 +193,7 @@ Medium medium_of(Store* s, int prec32) {
     m.dC = prec32 ? (const void*)s->dC32 : (const void*)s->dC64;
     m.drho = prec32 ? (const void*)s->drho32 : (const void*)s->drho64;
     m.timer = &s->timer;
+    m.kernel = s->kernel;
     return m;
 }
 
@@ -207,6 +209,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->max_outer = 8;
     o->taper = 0;
     o->graph = 1;
+    o->kernel = LSM_KERNEL_DIFF;
 }
 
 static lsm_status build_spectrum(lsm_t h) {
@@ -214,16 +217,18 @@ static lsm_status build_spectrum(lsm_t h) {
     const Dims& d = s->d;
     const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long P = (long long)d.Lx * d.Ly * d.Lz;
-    CK(h, cudaMalloc(&h->ghat64, 6 * NO * sizeof(double2)));
+    const long long planes = s->kernel == LSM_KERNEL_H ? 24 : 6;
+    CK(h, cudaMalloc(&h->ghat64, planes * NO * sizeof(double2)));
     double2* scratch = nullptr;
     CK(h, cudaMalloc(&scratch, 6 * P * sizeof(double2)));
-    cudaError_t e = launch_green_setup(d, s->pl64, s->lam, s->mu, s->rho, h->omega, s->green, scratch, h->ghat64, s->st, &h->nl);
+    cudaError_t e = launch_green_setup(d, s->pl64, s->lam, s->mu, s->rho, h->omega, s->green, s->kernel, scratch, h->ghat64,
+                                       s->st, &h->nl);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     cudaFree(scratch);
     if (e != cudaSuccess) return cuda_fail(h, e, "green spectrum setup");
     if (s->precision == LSM_MIXED) {
-        CK(h, cudaMalloc(&h->ghat32, 6 * NO * sizeof(float2)));
-        CK(h, launch_d2f((const double*)h->ghat64, (float*)h->ghat32, 12 * NO, s->st, &h->nl));
+        CK(h, cudaMalloc(&h->ghat32, planes * NO * sizeof(float2)));
+        CK(h, launch_d2f((const double*)h->ghat64, (float*)h->ghat32, 2 * planes * NO, s->st, &h->nl));
         CK(h, cudaStreamSynchronize(s->st));
     }
     return LSM_OK;
@@ -244,7 +249,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     if (opts) o = *opts;
     if ((o.precision != LSM_FP64 && o.precision != LSM_MIXED) || (o.green != LSM_GREEN_EXACT && o.green != LSM_GREEN_PAPER) ||
         !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1 || o.taper < 0 ||
-        (o.graph != 0 && o.graph != 1))
+        (o.graph != 0 && o.graph != 1) || (o.kernel != LSM_KERNEL_DIFF && o.kernel != LSM_KERNEL_H))
         return fail(nullptr, LSM_ERR_ARG, "lsm_create: invalid options");
     static bool attrs_done = false;
     if (!attrs_done) {
@@ -296,6 +301,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     CKB(cudaMemcpyAsync(s->dC64, dC, 21 * d.N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     CKB(cudaMemcpyAsync(s->drho64, drho, d.N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
     s->taper = o.taper;
+    s->kernel = o.kernel;
     CKB(launch_taper(d, s->taper, s->dC64, s->drho64, s->st, &h->nl));
     if (o.precision == LSM_MIXED) {
         CKB(cudaMalloc(&s->dC32, 21 * d.N * sizeof(float)));
@@ -425,6 +431,7 @@ extern "C" lsm_status lsm_apply_c64(lsm_t h, const void* u, void* Au) {
 extern "C" lsm_status lsm_adjoint(lsm_t h, const void* v, void* AHv) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_adjoint: null handle");
     if (!v || !AHv || v == AHv) return fail(h, LSM_ERR_ARG, "lsm_adjoint: v and AHv must be distinct non-null device buffers");
+    if (h->s->kernel == LSM_KERNEL_H) return fail(h, LSM_ERR_ARG, "lsm_adjoint: not available for LSM_KERNEL_H");
     return apply_one<double>(h, v, AHv, true);
 }
 
@@ -446,7 +453,7 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     cudaFree(w.block);
     w = SolverWS();
     long long e1, e2;
-    apply_ws_elems(s->d, &e1, &e2);
+    apply_ws_elems(s->d, s->kernel, &e1, &e2);
     const bool mixed = s->precision == LSM_MIXED;
     const size_t csz = mixed ? sizeof(float2) : sizeof(double2);
     const int nblk = vec_blocks(n3);
@@ -827,6 +834,7 @@ extern "C" lsm_status lsm_solve(lsm_t h, const void* b, void* x, int* iters, dou
 
 extern "C" lsm_status lsm_solve_adjoint(lsm_t h, const void* b, void* x, int* iters, double* relres) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_solve_adjoint: null handle");
+    if (h->s->kernel == LSM_KERNEL_H) return fail(h, LSM_ERR_ARG, "lsm_solve_adjoint: not available for LSM_KERNEL_H");
     const void* bb[1] = {b};
     void* xx[1] = {x};
     return solve_batched(1, &h, bb, xx, iters, relres, nullptr, true);
@@ -851,6 +859,7 @@ extern "C" lsm_status lsm_gradient(lsm_t h, const void* u, const void* lam, doub
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_gradient: null handle");
     if (!u || !lam || !gC || !grho) return fail(h, LSM_ERR_ARG, "lsm_gradient: null pointer argument");
     Store* s = h->s;
+    if (s->kernel == LSM_KERNEL_H) return fail(h, LSM_ERR_ARG, "lsm_gradient: not available for LSM_KERNEL_H");
     lsm_status rc = ensure_apply_ws(h);
     if (rc != LSM_OK) return rc;
     ApplySys<double> a;
@@ -972,7 +981,7 @@ static size_t static_apply_bytes(const int n[3]) {
     d.ex = d.nx + 2; d.ey = d.ny + 2; d.ez = d.nz + 2;
     d.N = (long long)d.nx * d.ny * d.nz;
     long long e1, e2;
-    apply_ws_elems(d, &e1, &e2);
+    apply_ws_elems(d, LSM_KERNEL_DIFF, &e1, &e2);
     return align_up(sizeof(ApplySys<double>)) + align_up(e1 * sizeof(double2)) + align_up(e2 * sizeof(double2));
 }
 
@@ -980,6 +989,7 @@ extern "C" lsm_status lsm_apply_static(lsm_t h, const void* u, void* Au) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_apply_static: null handle");
     if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply_static: u and Au must be distinct non-null device buffers");
     Store* s = h->s;
+    if (s->kernel == LSM_KERNEL_H) return fail(h, LSM_ERR_ARG, "lsm_apply_static: not available for LSM_KERNEL_H");
     const int n[3] = {s->d.nx, s->d.ny, s->d.nz};
     const size_t need = static_apply_bytes(n);
     if (need > STATIC_SCRATCH_BYTES) {
@@ -991,7 +1001,7 @@ extern "C" lsm_status lsm_apply_static(lsm_t h, const void* u, void* Au) {
     void* base = nullptr;
     CK(h, static_scratch_addr(&base));
     long long e1, e2;
-    apply_ws_elems(s->d, &e1, &e2);
+    apply_ws_elems(s->d, s->kernel, &e1, &e2);
     char* p = (char*)base;
     ApplySys<double>* dev_args = (ApplySys<double>*)p;
     double2* w1 = (double2*)(p + align_up(sizeof(ApplySys<double>)));

@@ -27,6 +27,7 @@ LSM_FP64 = 0
 LSM_MIXED = 1
 LSM_GREEN_EXACT = 0
 LSM_GREEN_PAPER = 1
+LSM_KERNEL_DIFF, LSM_KERNEL_H = 0, 1
 
 STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR_OOM", -4: "LSM_ERR_BREAKDOWN",
                 -5: "LSM_ERR_NOCONV", -6: "LSM_ERR_TIMEOUT", 1: "LSM_WARN_SOURCE_ON_NODE"}
@@ -40,7 +41,8 @@ EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", 
 
 class lsm_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("green", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
-                ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int), ("graph", ct.c_int)]
+                ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int), ("graph", ct.c_int),
+                ("kernel", ct.c_int)]
 
 
 class LSMError(RuntimeError):

@@ -48,6 +48,7 @@ def test_default_opts(lib):
     o = lsm.lsm_default_opts()
     assert o.precision == lsm.LSM_FP64 and o.green == lsm.LSM_GREEN_EXACT
     assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-6 and o.max_outer >= 2 and o.taper == 0
+    assert o.graph == 1 and o.kernel == lsm.LSM_KERNEL_DIFF
 
 
 @pytest.mark.parametrize("n,ok", [((2, 2, 2), True), ((1, 4, 4), False), ((7, 4, 4), False),
@@ -90,7 +91,7 @@ def test_bad_options_rejected(lib):
     arr = (ct.c_int * 3)(4, 4, 4)
     fake = ct.c_void_p(16)
     for kw in (dict(precision=7), dict(green=3), dict(tol=0.0), dict(maxit=0), dict(inner_tol=-1.0), dict(max_outer=0),
-               dict(taper=-2)):
+               dict(taper=-2), dict(graph=2), dict(kernel=2), dict(kernel=-1)):
         o = lsm.lsm_default_opts(**kw)
         code = lib.lsm_create(ct.byref(out), arr, 10.0, 1e9, 1e9, 2000.0, fake, fake, 1.0, ct.byref(o), None)
         assert code == lsm.LSM_ERR_ARG, kw
@@ -102,5 +103,6 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lsm_adjoint(None, None, None) == lsm.LSM_ERR_ARG
     assert lib.lsm_solve(None, None, None, None, None) == lsm.LSM_ERR_ARG
     assert lib.lsm_solve_batched(0, None, None, None, None, None, None) == lsm.LSM_ERR_ARG
+    assert lib.lsm_source_moments(None, 1, None, None, None) == lsm.LSM_ERR_ARG
     lib.lsm_destroy(None)
     assert lib.lsm_launch_count(None) == 0
