@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--systems", type=int, default=8, help="moment tensors solved together per step")
     ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
+    ap.add_argument("--kernel", default="diff", choices=["diff", "h"],
+                    help="operator form: difference form (default) or sampled analytic H (Eq. 21 literally)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
@@ -69,6 +71,39 @@ def stage_bytes(stage, n, b, c):
         3: 3 * ez * Ly * Lx * b + 6 * NO * b + 3 * nz * Ly * Lx * b,
         4: 3 * nz * Ly * Lx * b + 3 * nz * ny * Lx * b,
         5: 3 * nz * ny * Lx * b + 3 * N * b + 3 * N * b,
+    }[stage]
+
+
+def stage_bytes_h(stage, n, b, c):
+    """Algorithmic bytes of the sampled-H form's stages (9 transformed planes, 24 spectra)."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    Lx, Ly, Lz = 2 * nx, 2 * ny, 2 * nz
+    P = Lx * Ly * Lz
+    NO = (nx + 1) * (ny + 1) * (nz + 1)
+    return {
+        0: (15 * b + 22 * c) * N,
+        1: 9 * N * b + 9 * nz * ny * Lx * b,
+        2: 9 * nz * ny * Lx * b + 9 * nz * Ly * Lx * b,
+        3: 9 * nz * Ly * Lx * b + 9 * P * b + (9 * P + 24 * NO + 3 * P) * b + 3 * P * b + 3 * nz * Ly * Lx * b,
+        4: 3 * nz * Ly * Lx * b + 3 * nz * ny * Lx * b,
+        5: 3 * nz * ny * Lx * b + 3 * N * b + 3 * N * b,
+    }[stage]
+
+
+def stage_flops_h(stage, n):
+    import math
+    nx, ny, nz = n
+    N = nx * ny * nz
+    Lx, Ly, Lz = 2 * nx, 2 * ny, 2 * nz
+    fft = lambda L: 5.0 * L * math.log2(L)  # noqa: E731
+    return {
+        0: N * (9 * 2 + 36 * 4) + 3 * N * 2,
+        1: 9 * ny * nz * fft(Lx),
+        2: 9 * nz * Lx * fft(Ly),
+        3: (9 + 3) * Lx * Ly * fft(Lz) + Lx * Ly * Lz * (27 * 6 + 24 * 2),
+        4: 3 * nz * Lx * fft(Ly),
+        5: 3 * ny * nz * fft(Lx) + 3 * N * 2,
     }[stage]
 
 
@@ -279,7 +314,7 @@ def _config(args, wl, med):
     f = wl.freqs_hz
     return {"workload": wl.name if not args.grid else f"{wl.name}@{args.grid}", "grid": list(med.n), "dx_m": med.h,
             "frequencies_hz": f"{f[0]:g}-{f[-1]:g} ({len(f)})", "systems_per_step": args.systems,
-            "precision": args.precision, "tol": wl.tol, "parallelism": "replicas",
+            "precision": args.precision, "kernel": args.kernel, "tol": wl.tol, "parallelism": "replicas",
             "l2": "inputs larger than L2 (contrast, Green spectra and Krylov vectors exceed 126 MB)"}
 
 
@@ -308,7 +343,8 @@ def main():
     fidx = rank_frequencies(rank, world, steps_total, len(freqs))
     dC = torch.from_numpy(med.dC).cuda().contiguous()
     drho = torch.from_numpy(med.drho).cuda().contiguous()
-    opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000)
+    opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000,
+                                kernel=lsm.LSM_KERNEL_H if args.kernel == "h" else lsm.LSM_KERNEL_DIFF)
     if args.inner_tol:
         opts.inner_tol = args.inner_tol
     handles = {}
@@ -395,13 +431,14 @@ def main():
         name = STAGES[stage] + ("<float>" if f32 else "<double>")
         rec = {"kernel": name, "ms": round(st_ms[slot], 3), "launches": st_launch[slot],
                "share_of_step": round(st_ms[slot] / ms, 4)}
+        sb, sf = (stage_bytes_h, stage_flops_h) if args.kernel == "h" else (stage_bytes, stage_flops)
         if f32:
-            nbytes = stage_bytes(stage, med.n, 8, 4)
+            nbytes = sb(stage, med.n, 8, 4)
             ach = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
             rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": nbytes})
         else:
-            fl = stage_flops(stage, med.n)
+            fl = sf(stage, med.n)
             ach = fl * napp / (st_ms[slot] / 1e3) / 1e12
             rec.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                         "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
@@ -412,7 +449,7 @@ def main():
     if dom:
         prec_s = "mixed" if dom["kernel"].endswith("<float>") else "fp64"
         stage_id = [k for k, v in STAGES.items() if dom["kernel"].startswith(v)][0]
-        dom["traffic"] = traffic_from_profile(stage_id, prec_s, med.n)
+        dom["traffic"] = traffic_from_profile(stage_id, prec_s, med.n) if args.kernel == "diff" else None
         dom["peak_kind"] = peak_kind if dom["bound"] == "hbm" else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"
     roof = dom
 
@@ -451,7 +488,7 @@ def main():
     if prec == lsm.LSM_MIXED and not args.no_fp64_form and rank == 0:
         dC = torch.from_numpy(med.dC).cuda().contiguous()
         drho = torch.from_numpy(med.drho).cuda().contiguous()
-        o64 = lsm.lsm_default_opts(precision=lsm.LSM_FP64, tol=wl.tol, maxit=2000)
+        o64 = lsm.lsm_default_opts(precision=lsm.LSM_FP64, tol=wl.tol, maxit=2000, kernel=opts.kernel)
         h64 = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[-1]], o64)
         del dC, drho
         sources(h64, b)

@@ -42,6 +42,7 @@ template <typename T, bool INPLACE> struct FftBounds {
 struct GenericFFT {
     static constexpr bool INPLACE = false;
     static constexpr int TPL = 0;
+    static constexpr int A_ = 0, B_ = 0;
     template <int S, typename C>
     static __device__ __forceinline__ C* run(C* a, C* b, const FftPlan& p, int NL, int LD, const C* __restrict__ tw) {
         return fft_smem<S>(a, b, p, NL, LD, tw, threadIdx.x, blockDim.x);
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(
             return (xin && es >= 0 && es < in_count) ? src[es * plane] : czero<C>();
         };
         auto st_s = [&](int l, int k, C v) { s[k * NL + l] = v; };
-        fft4_io<A, B, -1, false, true, NL>(s, tw, threadIdx.x, ld_g, st_s, in_off + in_count);
+        fft4_io<A, B, -1, false, true, NL>(s, tw, threadIdx.x, ld_g, st_s);
         if (fresh) {
             cp_async_wait_all();
             __syncthreads();
@@ -343,6 +344,172 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(
         };
         fft4_io<A, B, 1, true, false, NL>(s, tw, threadIdx.x, ld_s, st_g);
         __syncthreads();  // the next system's forward step writes s
+    }
+}
+
+// Register-resident FP32 z pass for L = A * A.  Thread (lx, q) of a TX x A block owns column
+// x0 + lx and, for each of the three components, the step-1 DFT of t = q and the step-2 DFT of
+// k1 = q.  The forward step 2 leaves X[q + A k2] (k2 = 0..A-1) of all three components in its
+// registers: exactly the inputs the inverse transform's step 1 needs for t = q, and all three
+// components of the same frequencies, so the Green multiply runs in registers and each transform
+// crosses shared memory once.  A block serves its (kx tile, ky) column for every system of the
+// batch: the next system's input rows (only the nin rows that can be nonzero) are copied into
+// shared memory asynchronously while the current one is transformed, and the spectrum slice is
+// staged once per frequency, as in k4_fftz_green.
+template <bool CONJ, int A, int TX>
+__global__ void __launch_bounds__(TX * A, 4) k4z_reg(
+    Dims d, const float2* __restrict__ tw, const ApplySys<float>* __restrict__ sys, int nsys, int in_count, int in_off,
+    int out_count, int out_off, int src_sel, int dst_sel) {
+    typedef float2 C;
+    constexpr int L = A * A, NT = TX * A;
+    constexpr int E = 16;                                            // float2 per 128-byte bank row
+    constexpr int YS = A * TX + (((TX - A * TX) % E) + E) % E;       // row stride of Y[t][.]
+    const int nin = in_off + in_count;    // rows of a padded line that can be nonzero (<= L)
+    extern __shared__ unsigned char smem_raw[];
+    C* sY = reinterpret_cast<C*>(smem_raw);
+    C* sX = sY + A * YS;                  // [3][nin][TX] inputs of the system in flight
+    C* sG = sX + 3 * nin * TX;            // [6][nz+1][TX] spectrum slice: a warp's reads are contiguous
+    const int lx = threadIdx.x % TX;
+    const int q = threadIdx.x / TX;
+    const int ky = blockIdx.y;
+    const int x0 = blockIdx.x * TX;
+    const int kx = x0 + lx;
+    const bool xin = kx < d.Lx;
+    const int fy = ky <= d.ny ? ky : d.Ly - ky;
+    const unsigned my = ky > d.ny ? SIGN_BIT : 0u;
+    const unsigned mx = kx > d.nx ? SIGN_BIT : 0u;
+    const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const int GC = (d.nz + 1) * TX;
+    const int plane = d.Ly * d.Lx;        // < 2^18, so element offsets below fit in 32 bits
+    const bool half = q + A * (A / 2) >= nin;   // step-1 inputs a >= A/2 lie in the zero padding
+    auto running = [&](int j) { return !sys[j].run || *sys[j].run; };
+    auto next_running = [&](int j) {
+        while (j < nsys && !running(j)) ++j;
+        return j;
+    };
+    // copy the nin input rows of system j's column tile into sX (rows before in_off are zero)
+    auto prefetch = [&](int j) {
+        const ApplySys<float> P = sys[j];
+        const C* base = pick<C>(P, src_sel) + (long long)ky * d.Lx + x0;
+        for (int i = threadIdx.x; i < 3 * nin * TX; i += NT) {
+            const int l = i % TX;
+            const int r = i / TX;
+            const int e = r % nin;
+            const int c = r / nin;
+            const int es = e - in_off;
+            C* to = &sX[(c * nin + e) * TX + l];
+            if (x0 + l < d.Lx && es >= 0) cp_async_elem(to, base + (long long)c * in_count * plane + (long long)es * plane + l);
+            else *to = czero<C>();
+        }
+        cp_async_commit();
+    };
+    int si = next_running(0);
+    if (si < nsys) prefetch(si);
+    const C* staged = nullptr;
+    while (si < nsys) {
+        const ApplySys<float> S = sys[si];
+        const int sn = next_running(si + 1);
+        cp_async_wait_all();
+        __syncthreads();   // sX holds this system's rows; the previous system is done with sG and sY
+        const bool fresh = S.ghat != staged;
+        if (fresh) {
+            for (int i = threadIdx.x; i < (d.nz + 1) * 6 * TX; i += NT) {
+                const int l = i % TX;
+                const int r = i / TX;
+                const int c = r % 6;
+                const int fz = r / 6;
+                const int kxx = x0 + l;
+                if (kxx < d.Lx) {
+                    const int fx = kxx <= d.nx ? kxx : d.Lx - kxx;
+                    cp_async_elem(&sG[c * GC + fz * TX + l], S.ghat + c * NO + ((long long)fz * (d.ny + 1) + fy) * (d.nx + 1) + fx);
+                }
+            }
+            cp_async_commit();
+            staged = S.ghat;
+        }
+        C R[3][A];
+        // ---- forward transforms, one component at a time through sY
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            C v[A];
+            const C* xc = sX + c * nin * TX + lx;
+            if (half) {
+#pragma unroll
+                for (int a = 0; a < A / 2; ++a) {
+                    const int e = q + A * a;
+                    v[a] = e < nin ? xc[e * TX] : czero<C>();
+                }
+                dft_reg<A, -1, true>(v);
+            } else {
+#pragma unroll
+                for (int a = 0; a < A; ++a) {
+                    const int e = q + A * a;
+                    v[a] = e < nin ? xc[e * TX] : czero<C>();
+                }
+                dft_reg<A, -1>(v);
+            }
+            if (q) {
+#pragma unroll
+                for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[q * k1]));
+            }
+            __syncthreads();   // the previous reads of sY are done (and, at c = 2, every read of sX)
+            if (c == 2 && sn < nsys) prefetch(sn);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) sY[q * YS + k1 * TX + lx] = v[k1];
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < A; ++t) R[c][t] = sY[t * YS + q * TX + lx];
+            dft_reg<A, -1>(R[c]);   // R[c][k2] = X_c[q + A k2]
+        }
+        if (fresh) {
+            // the slice's group is complete; the prefetch committed after it may still be in flight
+            if (sn < nsys) cp_async_wait_group<1>();
+            else cp_async_wait_all();
+            __syncthreads();
+        }
+        // ---- Green multiply in registers
+        if (xin) {
+#pragma unroll
+            for (int k2 = 0; k2 < A; ++k2) {
+                const int kz = q + A * k2;
+                const int fz = kz <= d.nz ? kz : L - kz;
+                const unsigned mz = kz > d.nz ? SIGN_BIT : 0u;
+                const C* g = sG + fz * TX + lx;
+                const C G0 = g[0], G1 = g[GC], G2 = g[2 * GC];
+                const C G3 = flip_sign(g[3 * GC], my ^ mz);
+                const C G4 = flip_sign(g[4 * GC], mx ^ mz);
+                const C G5 = flip_sign(g[5 * GC], mx ^ my);
+                const C q0 = R[0][k2], q1 = R[1][k2], q2 = R[2][k2];
+                R[0][k2] = gdot3<CONJ>(G0, q0, G5, q1, G4, q2);
+                R[1][k2] = gdot3<CONJ>(G5, q0, G1, q1, G3, q2);
+                R[2][k2] = gdot3<CONJ>(G4, q0, G3, q1, G2, q2);
+            }
+        }
+        // ---- inverse transforms: step 1 of t = q takes R[c][a] as its input a
+        C* __restrict__ dst = pick<C>(S, dst_sel) + ky * d.Lx + kx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dft_reg<A, 1>(R[c]);
+            if (q) {
+#pragma unroll
+                for (int k1 = 1; k1 < A; ++k1) R[c][k1] = cmulc(R[c][k1], __ldg(&tw[q * k1]));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) sY[q * YS + k1 * TX + lx] = R[c][k1];
+            __syncthreads();
+            C v[A];
+#pragma unroll
+            for (int t = 0; t < A; ++t) v[t] = sY[t * YS + q * TX + lx];
+            dft_reg<A, 1>(v);
+            C* dc = dst + (long long)c * out_count * plane;
+#pragma unroll
+            for (int k2 = 0; k2 < A; ++k2) {
+                const int eo = q + A * k2 - out_off;
+                if (xin && eo >= 0 && eo < out_count) dc[eo * plane] = v[k2];
+            }
+        }
+        si = sn;
     }
 }
 
@@ -972,7 +1139,17 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
             const int GS = 6 * TX + (((TX - 6 * TX) % E) + E) % E;
             sm += (size_t)(d.nz + 1) * GS * sizeof(C);  // spectrum slice
         }
-        if constexpr (F::INPLACE) {
+        if constexpr (F::INPLACE && sizeof(T) == 4 && F::A_ == F::B_) {
+            constexpr int A = F::A_, TXR = 4;
+            constexpr int E = 16;
+            constexpr int YS = A * TXR + (((TXR - A * TXR) % E) + E) % E;
+            const size_t smr = ((size_t)A * YS + (size_t)3 * (in_off + in_count) * TXR + (size_t)6 * (d.nz + 1) * TXR) *
+                               sizeof(C);
+            smem_attr((const void*)k4z_reg<CONJ, A, TXR>, smr);
+            k4z_reg<CONJ, A, TXR><<<dim3(cdiv(d.Lx, TXR), d.Ly, 1), TXR * A, smr, st>>>(
+                d, (const float2*)pl.twz, (const ApplySys<float>*)sys, nsys, in_count, in_off, out_count, out_off,
+                src_sel, dst_sel);
+        } else if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, TXC = 4;
             smem_attr((const void*)k4_fftz_green<T, CONJ, A, B, TXC>, sm);
             k4_fftz_green<T, CONJ, A, B, TXC><<<dim3(cdiv(d.Lx, TXC), d.Ly, 1), th, sm, st>>>(

@@ -75,6 +75,10 @@ __device__ __forceinline__ void cp_async_elem(C* smem_dst, const C* gmem_src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// wait until at most N of the most recently committed groups are still in flight
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Grid geometry of one medium.  Model nodes n_a; padded periodic length L_a = 2 n_a;
 // extended contrast-source nodes e_a = n_a + 2 (nodes -1 .. n_a).
