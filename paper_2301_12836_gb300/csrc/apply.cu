@@ -369,8 +369,9 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
     C* sY = reinterpret_cast<C*>(smem_raw);
     C* sX = sY + A * YS;                  // [3][nin][TX] inputs of the system in flight
     C* sG = sX + 3 * nin * TX;            // [6][nz+1][TX] spectrum slice: a warp's reads are contiguous
+    C* sW = sG + 6 * (d.nz + 1) * TX;     // twiddles exp(-2 pi i k / L), k < L
     const int lx = threadIdx.x % TX;
-    const int q = threadIdx.x / TX;
+    const int q0 = threadIdx.x / TX;
     const int ky = blockIdx.y;
     const int x0 = blockIdx.x * TX;
     const int kx = x0 + lx;
@@ -381,7 +382,6 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
     const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const int GC = (d.nz + 1) * TX;
     const int plane = d.Ly * d.Lx;        // < 2^18, so element offsets below fit in 32 bits
-    const bool half = q + A * (A / 2) >= nin;   // step-1 inputs a >= A/2 lie in the zero padding
     auto running = [&](int j) { return !sys[j].run || *sys[j].run; };
     auto next_running = [&](int j) {
         while (j < nsys && !running(j)) ++j;
@@ -403,10 +403,16 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
         }
         cp_async_commit();
     };
+    for (int i = threadIdx.x; i < L; i += NT) sW[i] = tw[i];   // ordered before use by the loop's first barrier
     int si = next_running(0);
     if (si < nsys) prefetch(si);
     const C* staged = nullptr;
     while (si < nsys) {
+        // q re-read through an opaque move: everything derived from it (rows, offsets, masks,
+        // twiddle indices) is recomputed per system instead of held in registers across systems
+        int q;
+        asm volatile("mov.u32 %0, %1;" : "=r"(q) : "r"(q0));
+        const bool half = q + A * (A / 2) >= nin;   // step-1 inputs a >= A/2 lie in the zero padding
         const ApplySys<float> S = sys[si];
         const int sn = next_running(si + 1);
         cp_async_wait_all();
@@ -450,7 +456,7 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
             }
             if (q) {
 #pragma unroll
-                for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[q * k1]));
+                for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], lds_fresh(&sW[q * k1]));
             }
             __syncthreads();   // the previous reads of sY are done (and, at c = 2, every read of sX)
             if (c == 2 && sn < nsys) prefetch(sn);
@@ -492,7 +498,7 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
             dft_reg<A, 1>(R[c]);
             if (q) {
 #pragma unroll
-                for (int k1 = 1; k1 < A; ++k1) R[c][k1] = cmulc(R[c][k1], __ldg(&tw[q * k1]));
+                for (int k1 = 1; k1 < A; ++k1) R[c][k1] = cmulc(R[c][k1], lds_fresh(&sW[q * k1]));
             }
             __syncthreads();
 #pragma unroll
@@ -1143,8 +1149,8 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
             constexpr int A = F::A_, TXR = 4;
             constexpr int E = 16;
             constexpr int YS = A * TXR + (((TXR - A * TXR) % E) + E) % E;
-            const size_t smr = ((size_t)A * YS + (size_t)3 * (in_off + in_count) * TXR + (size_t)6 * (d.nz + 1) * TXR) *
-                               sizeof(C);
+            const size_t smr = ((size_t)A * YS + (size_t)3 * (in_off + in_count) * TXR + (size_t)6 * (d.nz + 1) * TXR +
+                                (size_t)A * A) * sizeof(C);
             smem_attr((const void*)k4z_reg<CONJ, A, TXR>, smr);
             k4z_reg<CONJ, A, TXR><<<dim3(cdiv(d.Lx, TXR), d.Ly, 1), TXR * A, smr, st>>>(
                 d, (const float2*)pl.twz, (const ApplySys<float>*)sys, nsys, in_count, in_off, out_count, out_off,

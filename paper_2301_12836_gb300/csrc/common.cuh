@@ -64,6 +64,15 @@ __device__ __forceinline__ C gdot3(C g0, C qa, C g1, C qb, C g2, C qc) {
     return mkc<C>(re, im);
 }
 
+// Shared-memory load the compiler may not merge with other loads of the same address or move:
+// re-reading a small table at every use costs less than holding it in registers.
+__device__ __forceinline__ float2 lds_fresh(const float2* p) {
+    float2 r;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(r.x), "=f"(r.y) : "r"(a));
+    return r;
+}
+
 // Asynchronous global -> shared copies (sm_80+ cp.async): 8- or 16-byte elements.
 template <typename C>
 __device__ __forceinline__ void cp_async_elem(C* smem_dst, const C* gmem_src) {
