@@ -253,6 +253,17 @@ lsm_status lsm_time_traces(int nf, double df, int ntr, const void *spectra, int 
 long long lsm_launch_count(lsm_t h);
 
 /*
+ * Diagnostic (no counterpart in the paper): conj(a) . b over n complex64
+ * elements, accumulated exactly as the mixed solver's FP32 BiCGSTAB inner
+ * products are (each FP32 product split exactly with an FMA, compensated FP32
+ * partial sums over 16 elements, FP64 totals and FP64 cross-thread sums).
+ *   a, b  device complex64, n elements; out host double[2] = (re, im)
+ * LSM_ERR_ARG for a null pointer or n < 0.  Allocates a small scratch buffer;
+ * synchronises the handle's stream.
+ */
+lsm_status lsm_dot_c64(lsm_t h, long long n, const void *a, const void *b, double out[2]);
+
+/*
  * Diagnostics for roofline measurement (no counterpart in the paper).
  * lsm_timer_start(h, enable): zero the totals and the executed-apply counters, and (enable != 0)
  * from now on record a CUDA event pair on the handle's stream around every launch of every stage

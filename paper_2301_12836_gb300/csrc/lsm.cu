@@ -891,6 +891,22 @@ extern "C" lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const voi
     return LSM_OK;
 }
 
+extern "C" lsm_status lsm_dot_c64(lsm_t h, long long n, const void* a, const void* b, double out[2]) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_dot_c64: null handle");
+    if (!a || !b || !out || n < 0) return fail(h, LSM_ERR_ARG, "lsm_dot_c64: null pointer or negative length");
+    Store* s = h->s;
+    const int nblk = vec_blocks(n);
+    double* scratch = nullptr;
+    CK(h, cudaMalloc(&scratch, (2 * (size_t)nblk + 2) * sizeof(double)));
+    cudaError_t e = launch_dot_c64((const float2*)a, (const float2*)b, n, scratch, nblk, scratch + 2 * nblk, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, scratch + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lsm_dot_c64");
+    h->nl += 2;
+    return LSM_OK;
+}
+
 extern "C" lsm_status lsm_timer_start(lsm_t h, int enable) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_timer_start: null handle");
     Store* s = h->s;

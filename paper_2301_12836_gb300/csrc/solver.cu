@@ -86,17 +86,83 @@ __device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
 }
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-// conj(a) b accumulated in FP64
-template <typename C>
-__device__ __forceinline__ void acc_dot(double& re, double& im, C a, C b) {
-    const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
-    re += ax * bx + ay * by;
-    im += ax * by - ay * bx;
+// Running inner-product sums of one thread, K of them.
+// FP64 vectors: FP64 sums of FP64 products.
+// FP32 vectors: each product of two FP32 numbers is split exactly into p = fl(a b) and
+// e = fma(a, b, -p) (p + e = a b); p enters a compensated FP32 pair (hi, lo) through TwoSum, whose
+// rounding error joins e in lo, and every FLUSH elements the pair is added to an FP64 total.
+// With at most 2 FLUSH products per sum between flushes, the partial pair is within about
+// (4 FLUSH)^2 / 2 * 2^-48 (< 1e-11) of the exact sum, relative to the sum of |products|; the
+// totals and the cross-thread reduction are FP64.  This keeps the reductions memory-bound
+// instead of bound by the FP64 pipe (one 64th of the FP32 rate on this part).
+template <typename C, int K> struct Sums;
+
+template <int K> struct Sums<double2, K> {
+    double d[K];
+    __device__ __forceinline__ Sums() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] = 0.0;
+    }
+    __device__ __forceinline__ void prod(int k, double a, double b) { d[k] = fma(a, b, d[k]); }
+    __device__ __forceinline__ void step() {}
+    __device__ __forceinline__ void finish(double (&out)[K]) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = d[k];
+    }
+};
+
+template <int K> struct Sums<float2, K> {
+    static constexpr int FLUSH = 16;
+    float hi[K], lo[K];
+    double d[K];
+    int cnt;
+    __device__ __forceinline__ Sums() : cnt(0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            hi[k] = lo[k] = 0.f;
+            d[k] = 0.0;
+        }
+    }
+    __device__ __forceinline__ void prod(int k, float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float t = __fadd_rn(hi[k], p);
+        const float bp = __fsub_rn(t, hi[k]);
+        const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        hi[k] = t;
+        lo[k] = __fadd_rn(lo[k], __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void flush() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            d[k] += (double)hi[k] + (double)lo[k];
+            hi[k] = lo[k] = 0.f;
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void step() {
+        if (++cnt == FLUSH) flush();
+    }
+    __device__ __forceinline__ void finish(double (&out)[K]) {
+        flush();
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = d[k];
+    }
+};
+
+// sums k (re) and k + 1 (im) += conj(a) b
+template <typename C, int K>
+__device__ __forceinline__ void acc_dot(Sums<C, K>& S, int k, C a, C b) {
+    S.prod(k, a.x, b.x);
+    S.prod(k, a.y, b.y);
+    S.prod(k + 1, a.x, b.y);
+    S.prod(k + 1, -a.y, b.x);
 }
-template <typename C>
-__device__ __forceinline__ void acc_nrm(double& s, C a) {
-    const double ax = a.x, ay = a.y;
-    s += ax * ax + ay * ay;
+// sum k += |a|^2
+template <typename C, int K>
+__device__ __forceinline__ void acc_nrm(Sums<C, K>& S, int k, C a) {
+    S.prod(k, a.x, a.x);
+    S.prod(k, a.y, a.y);
 }
 
 template <typename T>
@@ -107,17 +173,19 @@ __global__ void __launch_bounds__(VTH) k_bcg_init(const BcgVecs<T>* __restrict__
     const int sys = blockIdx.y;
     if (skip && skip[sys].done) return;
     const BcgVecs<T> V = vecs[sys];
-    double v[2] = {0.0, 0.0};
+    Sums<C, 2> acc;
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const C b = V.b[i];
         C r = b;
         if (!x_zero) r = csub(b, V.v[i]);
         V.r[i] = r;
         V.rh[i] = r;
-        acc_nrm(v[0], b);
-        acc_nrm(v[1], r);
+        acc_nrm(acc, 0, b);
+        acc_nrm(acc, 1, r);
+        acc.step();
     }
-    double tot[2];
+    double v[2], tot[2];
+    acc.finish(v);
     if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
         BcgState& S = st[sys];
         S.bnorm2 = tot[0];
@@ -158,10 +226,13 @@ __global__ void __launch_bounds__(VTH) k_bcg_alpha(const BcgVecs<T>* __restrict_
     const int sys = blockIdx.y;
     if (!st[sys].run_v) return;
     const BcgVecs<T> V = vecs[sys];
-    double v[2] = {0.0, 0.0};
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH)
-        acc_dot(v[0], v[1], V.rh[i], V.v[i]);
-    double tot[2];
+    Sums<C, 2> acc;
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        acc_dot(acc, 0, V.rh[i], V.v[i]);
+        acc.step();
+    }
+    double v[2], tot[2];
+    acc.finish(v);
     if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
         BcgState& S = st[sys];
         S.rv = make_double2(tot[0], tot[1]);
@@ -184,13 +255,15 @@ __global__ void __launch_bounds__(VTH) k_bcg_s(const BcgVecs<T>* __restrict__ ve
     if (!st[sys].active) return;
     const BcgVecs<T> V = vecs[sys];
     const C al = from_d2<C>(st[sys].alpha);
-    double v[1] = {0.0};
+    Sums<C, 1> acc;
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const C s = csub(V.r[i], cmul(al, V.v[i]));
         V.s[i] = s;
-        acc_nrm(v[0], s);
+        acc_nrm(acc, 0, s);
+        acc.step();
     }
-    double tot[1];
+    double v[1], tot[1];
+    acc.finish(v);
     if (grid_sum<1>(v, pt, sys, &st[sys].counter, tot)) {
         BcgState& S = st[sys];
         S.snorm2 = tot[0];
@@ -208,13 +281,15 @@ __global__ void __launch_bounds__(VTH) k_bcg_omega(const BcgVecs<T>* __restrict_
     const int sys = blockIdx.y;
     if (!st[sys].run_t) return;
     const BcgVecs<T> V = vecs[sys];
-    double v[3] = {0.0, 0.0, 0.0};
+    Sums<C, 3> acc;
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const C t = V.t[i];
-        acc_dot(v[0], v[1], t, V.s[i]);
-        acc_nrm(v[2], t);
+        acc_dot(acc, 0, t, V.s[i]);
+        acc_nrm(acc, 2, t);
+        acc.step();
     }
-    double tot[3];
+    double v[3], tot[3];
+    acc.finish(v);
     if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) {
         BcgState& S = st[sys];
         S.ts = make_double2(tot[0], tot[1]);
@@ -234,7 +309,7 @@ __global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ v
     const int half = st[sys].half;
     const C al = from_d2<C>(st[sys].alpha);
     const C om = from_d2<C>(st[sys].omega);
-    double v[3] = {0.0, 0.0, 0.0};
+    Sums<C, 3> acc;
     if (half) {
         for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH)
             V.x[i] = cadd(V.x[i], cmul(al, V.p[i]));
@@ -244,11 +319,13 @@ __global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ v
             V.x[i] = cadd(V.x[i], cadd(cmul(al, V.p[i]), cmul(om, s)));
             const C r = csub(s, cmul(om, t));
             V.r[i] = r;
-            acc_nrm(v[0], r);
-            acc_dot(v[1], v[2], V.rh[i], r);
+            acc_nrm(acc, 0, r);
+            acc_dot(acc, 1, V.rh[i], r);
+            acc.step();
         }
     }
-    double tot[3];
+    double v[3], tot[3];
+    acc.finish(v);
     if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) {
         BcgState& S = st[sys];
         S.iters += 1;
@@ -356,6 +433,38 @@ __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64
         x.y += sc * (double)d.y;
         X[i] = x;
     }
+}
+
+// conj(a) . b of complex64 vectors with the inner-product accumulation of the FP32 solver kernels:
+// per-block partials, summed in block order by k_dot_finish (diagnostic entry point).
+__global__ void __launch_bounds__(VTH) k_dot_c64(const float2* __restrict__ a, const float2* __restrict__ b, long long n,
+                                                 double* __restrict__ partial) {
+    Sums<float2, 2> acc;
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        acc_dot(acc, 0, a[i], b[i]);
+        acc.step();
+    }
+    double v[2];
+    acc.finish(v);
+    __shared__ double sh[32 * 2];
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = v[0];
+        partial[2 * blockIdx.x + 1] = v[1];
+    }
+}
+__global__ void k_dot_finish(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partial[2 * b + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+cudaError_t launch_dot_c64(const float2* a, const float2* b, long long n, double* partial, int nblk, double* out,
+                           cudaStream_t s) {
+    k_dot_c64<<<nblk, VTH, 0, s>>>(a, b, n, partial);
+    k_dot_finish<<<1, 32, 0, s>>>(partial, nblk, out);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -81,4 +81,9 @@ cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, long l
 
 int vec_blocks(long long n);
 
+// conj(a) . b over n complex64 elements with the FP32 solver's inner-product accumulation;
+// partial: 2 * nblk doubles of scratch, out: 2 doubles (device)
+cudaError_t launch_dot_c64(const float2* a, const float2* b, long long n, double* partial, int nblk, double* out,
+                           cudaStream_t s);
+
 }  // namespace lsm

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_source_moments", "lsm_apply", "lsm_apply_c64",
            "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
-           "lsm_source_gradient", "lsm_time_traces", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
+           "lsm_source_gradient", "lsm_time_traces", "lsm_dot_c64", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
 
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH):
     lib.lsm_source.restype = i
     lib.lsm_source_moments.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(d), ct.POINTER(vp)]
     lib.lsm_source_moments.restype = i
+    lib.lsm_dot_c64.argtypes = [vp, ct.c_longlong, vp, vp, ct.POINTER(d)]
+    lib.lsm_dot_c64.restype = i
     for name in ("lsm_apply", "lsm_apply_c64", "lsm_adjoint"):
         getattr(lib, name).argtypes = [vp, vp, vp]
         getattr(lib, name).restype = i
@@ -274,6 +276,16 @@ def lsm_time_traces(spectra: torch.Tensor, df, nt, dt, fp, t0, stream: torch.cud
 
 def lsm_launch_count(h: Handle) -> int:
     return int(load().lsm_launch_count(h.ptr))
+
+
+def lsm_dot_c64(h: Handle, a: torch.Tensor, b: torch.Tensor) -> complex:
+    """conj(a) . b of two complex64 device vectors with the mixed solver's inner-product accumulation."""
+    if a.numel() != b.numel():
+        raise ValueError("lsm_dot_c64: vectors of different lengths")
+    out = (ct.c_double * 2)()
+    n = a.numel()
+    _check(load().lsm_dot_c64(h.ptr, n, _ptr(a, torch.complex64, n), _ptr(b, torch.complex64, n), out), h.ptr)
+    return complex(out[0], out[1])
 
 
 def lsm_timer_start(h: Handle, enable: bool = True) -> None:

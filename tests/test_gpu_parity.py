@@ -73,6 +73,28 @@ def test_source_moments_on_node_and_bad_arguments():
         lsm.lsm_source_moments(h, [], [1.0, 2.0, 3.0], [])
 
 
+@pytest.mark.parametrize("n", [1, 4097, 3 * 1000003])
+def test_fp32_inner_products_are_fp64_accurate(n):
+    """The FP32 solver's inner products (exact products, compensated partial sums, FP64 totals)
+    against the correctly rounded sum of the exact products (math.fsum of FP64 products of the
+    FP32 values, which are exact): error <= 1e-11 of sum |terms|, including a sum that cancels."""
+    import math
+    med = sy.random_medium((4, 4, 4), h=10.0, seed=25)
+    h = handle(med, W, precision=lsm.LSM_MIXED)
+    rng = np.random.default_rng(n)
+    a = ((rng.standard_normal(n) + 1j * rng.standard_normal(n)) * np.exp(3 * rng.standard_normal(n))).astype(np.complex64)
+    b = ((rng.standard_normal(n) + 1j * rng.standard_normal(n)) * np.exp(3 * rng.standard_normal(n))).astype(np.complex64)
+    for bb in (b, (1j * a).astype(np.complex64)):        # i a: the real part cancels exactly
+        ax, ay = a.real.astype(np.float64), a.imag.astype(np.float64)
+        bx, by = bb.real.astype(np.float64), bb.imag.astype(np.float64)
+        re_terms = np.concatenate([ax * bx, ay * by])
+        im_terms = np.concatenate([ax * by, -ay * bx])
+        got = lsm.lsm_dot_c64(h, dev(a), dev(bb))
+        for g, terms in ((got.real, re_terms), (got.imag, im_terms)):
+            exact = math.fsum(terms)
+            assert abs(g - exact) <= 1e-11 * np.abs(terms).sum() + 1e-300, (g, exact)
+
+
 def test_source_on_node_flag():
     med = sy.random_medium((6, 6, 6), h=10.0, seed=22)
     h = handle(med, W)
