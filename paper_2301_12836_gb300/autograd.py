@@ -23,10 +23,12 @@ class ReceiverModel:
     n: (nx, ny, nz); dx [m]; lam0, mu0, rho0: background; freqs_hz: frequencies; xs: source
     position [m]; receivers: integer tensor/array (k, 3) of node indices (ix, iy, iz).
     dC0, drho0: an initial contrast (device float64) used to create the handles.
+    checkpoint: keep no wavefield between forward and backward; the backward pass solves the
+    forward systems again (twice the forward solves, nf * 3N complex values less memory).
     """
 
     def __init__(self, n, dx, lam0, mu0, rho0, dC0, drho0, freqs_hz, xs, receivers, precision=lsm.LSM_FP64,
-                 tol=1e-10, maxit=2000):
+                 tol=1e-10, maxit=2000, checkpoint=False):
         import numpy as np
         self.n = tuple(int(v) for v in n)
         nx, ny, nz = self.n
@@ -39,10 +41,20 @@ class ReceiverModel:
         rec = torch.as_tensor(np.asarray(receivers), dtype=torch.long)
         self.ridx = (rec[:, 2] * ny * nx + rec[:, 1] * nx + rec[:, 0]).to(dC0.device)
         self.device = dC0.device
+        self.checkpoint = bool(checkpoint)
         self.last_iters = []
 
     def __call__(self, dC, drho, M):
         return _LSReceivers.apply(dC, drho, M, self)
+
+
+def _forward_field(model, h, Mv):
+    """u solving A u = u0(M) at the handle's frequency (from a zero initial guess)."""
+    b = torch.empty(3 * model.N, dtype=torch.complex128, device=model.device)
+    lsm.lsm_source(h, Mv, model.xs, b)
+    x = torch.zeros_like(b)
+    _, model._it, _ = lsm.lsm_solve(h, b, x)
+    return x
 
 
 class _LSReceivers(torch.autograd.Function):
@@ -58,15 +70,14 @@ class _LSReceivers(torch.autograd.Function):
         us = []
         model.last_iters = []
         for f, h in enumerate(model.handles):
-            b = torch.empty(3 * N, dtype=torch.complex128, device=model.device)
-            lsm.lsm_source(h, Mv, model.xs, b)
-            x = torch.zeros_like(b)
-            _, it, _ = lsm.lsm_solve(h, b, x)
-            model.last_iters.append(it)
-            us.append(x)
+            x = _forward_field(model, h, Mv)
+            model.last_iters.append(model._it)
+            if not model.checkpoint:
+                us.append(x)
             out[f] = x.view(3, N)[:, model.ridx].transpose(0, 1)
         ctx.model = model
         ctx.us = us
+        ctx.Mv = Mv
         ctx.save_for_backward(dC, drho)
         return out
 
@@ -85,6 +96,7 @@ class _LSReceivers(torch.autograd.Function):
             rhs.view(3, N)[:, model.ridx] = g[f].transpose(0, 1)
             lam = torch.zeros_like(rhs)
             lsm.lsm_solve_adjoint(h, rhs, lam)
-            lsm.lsm_gradient(h, ctx.us[f], lam, gC, grho, accumulate=True)
+            u = _forward_field(model, h, ctx.Mv) if model.checkpoint else ctx.us[f]
+            lsm.lsm_gradient(h, u, lam, gC, grho, accumulate=True)
             gM += torch.tensor(lsm.lsm_source_gradient(h, model.xs, lam), dtype=torch.float64)
         return gC.view_as(dC), grho.view_as(drho), gM.to(dtype=torch.float64), None

@@ -110,6 +110,26 @@ def test_autograd_gradient_vs_finite_differences_and_oracle(shape, freqs, seed):
         assert rel(host(gr).reshape(wr.shape), wr) < 1e-8
 
 
+def test_checkpointed_backward_matches_stored_fields():
+    """checkpoint=True re-solves the forward systems in backward; the solves are deterministic,
+    so the gradients are bitwise those of the stored-field backward."""
+    med = sy.random_medium((12, 10, 9), h=10.0, seed=58, frac=0.08)
+    rng = np.random.default_rng(58)
+    rec = np.stack([rng.integers(0, 12, 5), rng.integers(0, 10, 5), np.zeros(5, dtype=int)], axis=1)
+    xs = np.array([51.3, 44.1, 40.7])
+    grads = []
+    for ck in (False, True):
+        model = ReceiverModel(med.n, med.h, med.lam0, med.mu0, med.rho0, dev(med.dC), dev(med.drho), (7.0, 12.0), xs,
+                              rec, tol=1e-12, checkpoint=ck)
+        dC = dev(med.dC).requires_grad_(True)
+        drho = dev(med.drho).requires_grad_(True)
+        M = torch.tensor(sy.double_couple_13(), dtype=torch.float64, requires_grad=True)
+        torch.sum(torch.abs(model(dC, drho, M)) ** 2).backward()
+        grads.append((dC.grad.clone(), drho.grad.clone(), M.grad.clone()))
+    for a, b in zip(*grads):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.slow
 def test_adjoint_workload_96_surface_receivers():
     """96^3 Table-2 layers + 3% random perturbation, dip-slip source, 256 surface receivers
