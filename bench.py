@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
     ap.add_argument("--kernel", default="diff", choices=["diff", "h"],
                     help="operator form: difference form (default) or sampled analytic H (Eq. 21 literally)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default FFT schedule (no autotuning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
@@ -355,6 +356,10 @@ def main():
         if i not in handles:
             handles[i] = lsm.lsm_create_shared(base, 2 * np.pi * freqs[i])
     del dC, drho
+    schedule = None
+    if not args.no_tune:
+        v64, v32 = lsm.lsm_autotune(base, nsys, 2)
+        schedule = {"fp64": v64, "fp32": v32}
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     N3 = 3 * base.N
@@ -463,6 +468,7 @@ def main():
         "iterations_mean": round(float(np.mean(stats["iters"])), 2),
         "relres_max": float(np.max(stats["relres"])),
         "setup_s": round(t_setup, 2),
+        "schedule": schedule,
         "roofline": roof, "stages": stages, "gpu_launches": int(launches_all),
     }
     cs = sampler.summary()
@@ -491,6 +497,8 @@ def main():
         o64 = lsm.lsm_default_opts(precision=lsm.LSM_FP64, tol=wl.tol, maxit=2000, kernel=opts.kernel)
         h64 = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[-1]], o64)
         del dC, drho
+        if schedule is not None:
+            lsm.lsm_set_schedule(h64, lsm.LSM_FP64, schedule["fp64"])
         sources(h64, b)
         for j in range(nsys):
             x[j].zero_()

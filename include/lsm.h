@@ -253,6 +253,34 @@ lsm_status lsm_time_traces(int nf, double df, int ntr, const void *spectra, int 
 long long lsm_launch_count(lsm_t h);
 
 /*
+ * FFT schedules (no counterpart in the paper).  Each apply stage can run one of
+ * a few kernel variants: v[0] (strain + contraction) is always 0; v[1] forward
+ * x pass, v[2] forward y pass, v[4] inverse y pass, v[5] inverse x pass and
+ * epilogue: 0 = compile-time two-step FFT where the line length allows it
+ * (16..256), 1 = runtime mixed-radix Stockham engine, 2 = the same with half
+ * its tile; v[3] z pass with the Green multiply: 0..2 as above (0 is the
+ * register-resident kernel in FP32), 3 = the shared-memory two-step kernel.
+ * Every variant computes the same operator.  precision: LSM_FP64 (the FP64
+ * applies) or LSM_MIXED (the FP32 applies of a mixed handle).  The schedule
+ * belongs to the medium (all handles sharing it); setting one drops the
+ * captured iteration graphs.  LSM_ERR_ARG for an invalid variant.
+ */
+lsm_status lsm_set_schedule(lsm_t h, int precision, const int v[6]);
+lsm_status lsm_get_schedule(lsm_t h, int precision, int v[6]);
+
+/*
+ * The project's tuner: times `reps` batched applies (1..100) of nsys systems
+ * (1..64, the batch size the solves will use) under every variant set, per
+ * precision the handle runs, with CUDA events around each stage, and keeps for
+ * every stage the fastest variant.  The chosen schedules are returned in v64
+ * and v32 (host int[6] each, may be NULL; v32 is all 0 for an LSM_FP64
+ * handle).  Sizes the solver workspace for nsys systems and allocates 1 + nsys
+ * 3N complex128 buffers for the duration; resets the stage timer's totals;
+ * synchronises the stream.
+ */
+lsm_status lsm_autotune(lsm_t h, int nsys, int reps, int v64[6], int v32[6]);
+
+/*
  * Diagnostic (no counterpart in the paper): conj(a) . b over n complex64
  * elements, accumulated exactly as the mixed solver's FP32 BiCGSTAB inner
  * products are (each FP32 product split exactly with an FMA, compensated FP32

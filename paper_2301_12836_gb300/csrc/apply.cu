@@ -952,19 +952,22 @@ static int rows_per_tile(int L) {
     while (B > 1 && 2 * (size_t)L * (3 * B + 1) * sizeof(C) > SMEM_CAP) --B;
     return B;
 }
+// Tiles of the generic engine; shrink halves them (a schedule variant, see Schedule).
 template <typename T>
-static int strided_tx(int L, int ncomp) {
+static int strided_tx(int L, int ncomp, int shrink = 0) {
     typedef typename cplx_of<T>::type C;
     int TX = sizeof(T) == 4 ? 16 : 8;
     while (TX > 1 && 2 * (size_t)L * ncomp * TX * sizeof(C) > SMEM_CAP) TX /= 2;
-    return TX;
+    TX >>= shrink;
+    return TX > 1 ? TX : 1;
 }
 template <typename T>
-static int generic_rows_nl(int L) {
+static int generic_rows_nl(int L, int shrink = 0) {
     typedef typename cplx_of<T>::type C;
     int NL = 16;
     while (NL > 1 && 2 * (size_t)L * (NL + 1) * sizeof(C) > SMEM_CAP) NL /= 2;
-    return NL;
+    NL >>= shrink;
+    return NL > 1 ? NL : 1;
 }
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -994,9 +997,14 @@ static void smem_attr(const void* k, size_t sm) {
     seen.push_back({k, sm});
 }
 
-// Call fn with the FFT engine for line length L: compile-time four-step for 16..256, else generic.
+// Call fn with the FFT engine for line length L: compile-time four-step for 16..256 unless the
+// schedule variant v asks for the generic engine (v = 1, 2), else generic.
 template <typename Fn>
-static void with_engine(int L, Fn&& fn) {
+static void with_engine(int L, Fn&& fn, int v = 0) {
+    if (v == 1 || v == 2) {
+        fn(GenericFFT());
+        return;
+    }
     switch (L) {
         case 16: fn(FourStepFFT<4, 4>()); break;
         case 32: fn(FourStepFFT<4, 8>()); break;
@@ -1009,21 +1017,22 @@ static void with_engine(int L, Fn&& fn) {
 
 // tile of B rows x 3 components for the contiguous x passes
 template <typename T, class F>
-static void rows_cfg(int L, int& B, int& threads, size_t& sm) {
+static void rows_cfg(int L, int& B, int& threads, size_t& sm, int shrink = 0) {
     typedef typename cplx_of<T>::type C;
     if constexpr (F::INPLACE) {
         B = sizeof(T) == 4 ? 8 : 4;
         threads = 3 * B * F::TPL;
         sm = (size_t)L * (3 * B + 1) * sizeof(C);
     } else {
-        B = rows_per_tile<T>(L);
+        B = rows_per_tile<T>(L) >> shrink;
+        if (B < 1) B = 1;
         threads = NTH;
         sm = 2 * (size_t)L * (3 * B + 1) * sizeof(C);
     }
 }
 // tile of TX consecutive lines x ncomp components for the strided passes
 template <typename T, class F>
-static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm) {
+static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm, int shrink = 0) {
     typedef typename cplx_of<T>::type C;
     if constexpr (F::INPLACE) {
         TX = sizeof(T) == 4 ? (ncomp == 1 ? 16 : 4) : (ncomp == 1 ? 8 : 4);
@@ -1031,7 +1040,7 @@ static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm) {
         const size_t ybuf = (size_t)F::B_ * fft4_ystride<F::A_, C>(ncomp * TX);
         sm = (ybuf > (size_t)L * ncomp * TX ? ybuf : (size_t)L * ncomp * TX) * sizeof(C);
     } else {
-        TX = strided_tx<T>(L, ncomp);
+        TX = strided_tx<T>(L, ncomp, shrink);
         threads = NTH;
         sm = 2 * (size_t)L * ncomp * TX * sizeof(C);
     }
@@ -1039,7 +1048,7 @@ static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm) {
 
 // forward x FFT of the contrast source rows: w2 [3][ez][ey][ex] -> w1 [3][ez][ey][Lx]
 template <typename T>
-static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, cudaStream_t st) {
+static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, cudaStream_t st, int v = 0) {
     typedef typename cplx_of<T>::type C;
     const long long nrows = 3LL * d.ez * d.ey;
     with_engine(d.Lx, [&](auto eng) {
@@ -1051,18 +1060,19 @@ static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const P
             k4_rows<T, -1, A, B, NL><<<dim3(cdiv(nrows, NL), nsys), NL * F::TPL, sm, st>>>(
                 (const C*)pl.twx, sys, 3, 2, nrows, d.ex, 0, d.Lx, 0);
         } else {
-            const int NL = generic_rows_nl<T>(d.Lx);
+            const int NL = generic_rows_nl<T>(d.Lx, v == 2);
             const size_t sm = 2 * (size_t)d.Lx * (NL + 1) * sizeof(C);
             smem_attr((const void*)k_rows<T, -1>, sm);
             k_rows<T, -1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, (const C*)pl.twx, sys, 3, 2, nrows, NL,
                                                                          d.ex, 0, d.Lx, 0);
         }
-    });
+    }, v);
 }
 
 // xoff: padded-grid index of model node 0 (1 when the convolved source lives on the extended nodes)
 template <typename T>
-static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int xoff, cudaStream_t st) {
+static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int xoff, cudaStream_t st,
+                            int v = 0) {
     typedef typename cplx_of<T>::type C;
     with_engine(d.Lx, [&](auto eng) {
         using F = decltype(eng);
@@ -1075,24 +1085,24 @@ static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, con
         } else {
             int B, th;
             size_t sm;
-            rows_cfg<T, F>(d.Lx, B, th, sm);
+            rows_cfg<T, F>(d.Lx, B, th, sm, v == 2);
             smem_attr((const void*)k_fftx_out<T, F>, sm);
             k_fftx_out<T, F><<<dim3(cdiv(d.ny, B), d.nz, nsys), th, sm, st>>>(d, sys, pl.px, (const C*)pl.twx, B, xoff);
         }
-    });
+    }, v);
 }
 
 // Plain FFT of lines of length L along a strided axis: a.ncomp components per system, lines along
 // x (a.nlines of them), `outer` line groups (blockIdx.y) per component.
 template <typename T, int DIR>
 static void launch_strided(int L, const FftPlan& p, const void* tw, StridedArgs a, int outer, const ApplySys<T>* sys,
-                           int nsys, cudaStream_t st) {
+                           int nsys, cudaStream_t st, int v = 0) {
     typedef typename cplx_of<T>::type C;
     with_engine(L, [&](auto eng) {
         using F = decltype(eng);
         int th;
         size_t sm;
-        strided_cfg<T, F>(L, 1, a.TX, th, sm);
+        strided_cfg<T, F>(L, 1, a.TX, th, sm, v == 2);
         if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, TXC = sizeof(T) == 4 ? 16 : 8;
             smem_attr((const void*)k4_strided<T, DIR, A, B, TXC>, sm);
@@ -1101,20 +1111,21 @@ static void launch_strided(int L, const FftPlan& p, const void* tw, StridedArgs 
             smem_attr((const void*)k_strided<T, DIR, F>, sm);
             k_strided<T, DIR, F><<<dim3(cdiv(a.nlines, a.TX), outer, a.ncomp * nsys), th, sm, st>>>(p, (const C*)tw, a, sys);
         }
-    });
+    }, v);
 }
 
 // y pass over `planes` planes: src [ncomp][planes][in_count][Lx] (sel) -> dst [ncomp][planes][out_count][Lx] (sel)
 template <typename T, int DIR>
 static void launch_ypass(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int planes, int in_count,
-                         int in_off, int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st, int ncomp = 3) {
+                         int in_off, int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st, int ncomp = 3,
+                         int v = 0) {
     StridedArgs a;
     a.nlines = d.Lx;
     a.in_count = in_count; a.in_off = in_off; a.out_count = out_count; a.out_off = out_off;
     a.src_es = d.Lx; a.src_os1 = (long long)in_count * d.Lx; a.src_os2 = (long long)planes * in_count * d.Lx;
     a.dst_es = d.Lx; a.dst_os1 = (long long)out_count * d.Lx; a.dst_os2 = (long long)planes * out_count * d.Lx;
     a.ncomp = ncomp; a.src_sel = src_sel; a.dst_sel = dst_sel;
-    launch_strided<T, DIR>(d.Ly, pl.py, pl.twy, a, planes, sys, nsys, st);
+    launch_strided<T, DIR>(d.Ly, pl.py, pl.twy, a, planes, sys, nsys, st, v);
 }
 
 // plain z pass: src [ncomp][in_count][Ly][Lx] (sel) -> dst [ncomp][out_count][Ly][Lx] (sel)
@@ -1131,21 +1142,24 @@ static void launch_zplain(const Dims& d, const ApplySys<T>* sys, int nsys, const
     launch_strided<T, DIR>(d.Lz, pl.pz, pl.twz, a, d.Ly, sys, nsys, st);
 }
 
+// schedule variant v: 0 default (register-resident kernel for FP32 and L = A * A), 1 / 2 generic
+// engine (default / half tile), 3 the shared-memory four-step kernel for every precision
 template <typename T, bool CONJ>
 static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int in_count, int in_off,
-                         int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st) {
+                         int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st, int v = 0) {
     typedef typename cplx_of<T>::type C;
     with_engine(d.Lz, [&](auto eng) {
         using F = decltype(eng);
         int TX, th;
         size_t sm;
-        strided_cfg<T, F>(d.Lz, 3, TX, th, sm);
+        strided_cfg<T, F>(d.Lz, 3, TX, th, sm, v == 2);
         if constexpr (F::INPLACE) {
             const int E = (int)(128 / sizeof(C));
             const int GS = 6 * TX + (((TX - 6 * TX) % E) + E) % E;
             sm += (size_t)(d.nz + 1) * GS * sizeof(C);  // spectrum slice
         }
         if constexpr (F::INPLACE && sizeof(T) == 4 && F::A_ == F::B_) {
+          if (v != 3) {
             constexpr int A = F::A_, TXR = 4;
             constexpr int E = 16;
             constexpr int YS = A * TXR + (((TXR - A * TXR) % E) + E) % E;
@@ -1155,7 +1169,10 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
             k4z_reg<CONJ, A, TXR><<<dim3(cdiv(d.Lx, TXR), d.Ly, 1), TXR * A, smr, st>>>(
                 d, (const float2*)pl.twz, (const ApplySys<float>*)sys, nsys, in_count, in_off, out_count, out_off,
                 src_sel, dst_sel);
-        } else if constexpr (F::INPLACE) {
+            return;
+          }
+        }
+        if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, TXC = 4;
             smem_attr((const void*)k4_fftz_green<T, CONJ, A, B, TXC>, sm);
             k4_fftz_green<T, CONJ, A, B, TXC><<<dim3(cdiv(d.Lx, TXC), d.Ly, 1), th, sm, st>>>(
@@ -1165,7 +1182,7 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
             k_fftz_green<T, CONJ, F><<<dim3(cdiv(d.Lx, TX), d.Ly, nsys), th, sm, st>>>(
                 d, pl.pz, (const C*)pl.twz, sys, TX, in_count, in_off, out_count, out_off, src_sel, dst_sel);
         }
-    });
+    }, v);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1318,23 +1335,23 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
     // 2. contrast source on the extended nodes -> w2 [3][ez][ey][ex]; forward x FFT -> w1 [3][ez][ey][Lx]
     ktimer_mark(tm, 1, f32, st, 0);
     k_divq<T><<<dim3(grid_elems((long long)d.ex * d.ey * d.ez), nsys), NTH, 0, st>>>(d, drho, sys);
-    launch_xfwd<T>(d, sys, nsys, pl, st);
+    launch_xfwd<T>(d, sys, nsys, pl, st, m.sched[1]);
     ktimer_mark(tm, 1, f32, st, 1);
     // 3. forward y FFT: w1 [3][ez][ey][Lx] -> w2 [3][ez][Ly][Lx]
     ktimer_mark(tm, 2, f32, st, 0);
-    launch_ypass<T, -1>(d, sys, nsys, pl, d.ez, d.ey, 0, d.Ly, 0, 2, 3, st);
+    launch_ypass<T, -1>(d, sys, nsys, pl, d.ez, d.ey, 0, d.Ly, 0, 2, 3, st, 3, m.sched[2]);
     ktimer_mark(tm, 2, f32, st, 1);
     // 4. z FFT, Green multiply, inverse z FFT, crop: w2 [3][ez][Ly][Lx] -> w1 [3][nz][Ly][Lx]
     ktimer_mark(tm, 3, f32, st, 0);
-    launch_zpass<T, false>(d, sys, nsys, pl, d.ez, 0, d.nz, 1, 3, 2, st);
+    launch_zpass<T, false>(d, sys, nsys, pl, d.ez, 0, d.nz, 1, 3, 2, st, m.sched[3]);
     ktimer_mark(tm, 3, f32, st, 1);
     // 5. inverse y FFT + crop: w1 [3][nz][Ly][Lx] -> w2 [3][nz][ny][Lx]
     ktimer_mark(tm, 4, f32, st, 0);
-    launch_ypass<T, 1>(d, sys, nsys, pl, d.nz, d.Ly, 0, d.ny, 1, 2, 3, st);
+    launch_ypass<T, 1>(d, sys, nsys, pl, d.nz, d.Ly, 0, d.ny, 1, 2, 3, st, 3, m.sched[4]);
     ktimer_mark(tm, 4, f32, st, 1);
     // 6. inverse x FFT + crop + Au = u - u_s (reads w2)
     ktimer_mark(tm, 5, f32, st, 0);
-    launch_fftx_out<T>(d, sys, nsys, pl, 1, st);
+    launch_fftx_out<T>(d, sys, nsys, pl, 1, st, m.sched[5]);
     ktimer_mark(tm, 5, f32, st, 1);
     if (nl) *nl += 7;
     return cudaGetLastError();

@@ -42,6 +42,7 @@ struct Medium {
     const void* drho;    // [N] of T
     KTimer* timer;       // optional stage timer
     int kernel;          // 0: difference form (6 spectra); 1: sampled-H form (24 spectra)
+    int sched[6];        // FFT schedule variant per apply stage (0 default; see the pass launchers)
 };
 
 struct Plans {

@@ -69,6 +69,7 @@ struct Store {
     int precision = LSM_FP64, green = LSM_GREEN_EXACT;
     int taper = 0;
     int kernel = LSM_KERNEL_DIFF;
+    int sched[2][6] = {{0}};   // FFT schedule variant per apply stage, [FP64, FP32]
     cudaStream_t st = nullptr;
     double* dC64 = nullptr;
     double* drho64 = nullptr;
@@ -194,6 +195,7 @@ Medium medium_of(Store* s, int prec32) {
     m.drho = prec32 ? (const void*)s->drho32 : (const void*)s->drho64;
     m.timer = &s->timer;
     m.kernel = s->kernel;
+    for (int k = 0; k < 6; ++k) m.sched[k] = s->sched[prec32 ? 1 : 0][k];
     return m;
 }
 
@@ -519,6 +521,12 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     }
     return LSM_OK;
 }
+
+}  // namespace
+
+lsm_status tune_workspace(lsm_t h, int nsys) { return ensure_solver_ws(h, nsys); }
+
+namespace {
 
 // A (adjoint = false) or A^H (adjoint = true) for nsys systems
 template <typename T>
@@ -891,6 +899,150 @@ extern "C" lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const voi
     return LSM_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// FFT schedules and the tuner
+// ---------------------------------------------------------------------------------------------
+static bool schedule_ok(const int v[6]) {
+    if (v[0] != 0) return false;
+    for (int k = 1; k < 6; ++k)
+        if (v[k] < 0 || v[k] > (k == 3 ? 3 : 2)) return false;
+    return true;
+}
+
+static lsm_status timer_events(lsm_t h) {
+    KTimer& t = h->s->timer;
+    if (t.ev) return LSM_OK;
+    t.cap = 4096;
+    t.ev = new cudaEvent_t[2 * t.cap];
+    t.tag = new int[t.cap];
+    for (int i = 0; i < 2 * t.cap; ++i) CK(h, cudaEventCreate(&t.ev[i]));
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_set_schedule(lsm_t h, int precision, const int v[6]) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_set_schedule: null handle");
+    if (!v || (precision != LSM_FP64 && precision != LSM_MIXED) || !schedule_ok(v))
+        return fail(h, LSM_ERR_ARG, "lsm_set_schedule: invalid precision or variants");
+    Store* s = h->s;
+    CK(h, cudaStreamSynchronize(s->st));
+    for (int k = 0; k < 6; ++k) s->sched[precision == LSM_MIXED ? 1 : 0][k] = v[k];
+    drop_graphs(s->ws);   // captured iterations hold the old kernels
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_get_schedule(lsm_t h, int precision, int v[6]) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_get_schedule: null handle");
+    if (!v || (precision != LSM_FP64 && precision != LSM_MIXED))
+        return fail(h, LSM_ERR_ARG, "lsm_get_schedule: invalid arguments");
+    for (int k = 0; k < 6; ++k) v[k] = h->s->sched[precision == LSM_MIXED ? 1 : 0][k];
+    return LSM_OK;
+}
+
+// declared with the solver workspace below
+lsm_status tune_workspace(lsm_t h, int nsys);
+
+// Times `reps` batched applies of nsys systems (one shared input, separate outputs and
+// workspaces, the solver's layout) under each variant set and keeps the fastest variant per stage.
+template <typename T>
+static lsm_status tune_one(lsm_t h, int nsys, int reps, const void* u, void* out, int best[6]) {
+    typedef typename cplx_of<T>::type C;
+    Store* s = h->s;
+    SolverWS& w = s->ws;
+    KTimer& t = s->timer;
+    const bool f32 = sizeof(T) == 4;
+    const int p = f32 ? 1 : 0;
+    std::vector<ApplySys<T>> a(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        a[i].u = (const C*)u;
+        a[i].out = (C*)((char*)out + (size_t)i * 3 * s->d.N * sizeof(C));
+        a[i].ghat = f32 ? (const C*)h->ghat32 : (const C*)h->ghat64;
+        const bool fp64_of_mixed = !f32 && s->precision == LSM_MIXED;
+        a[i].w1 = fp64_of_mixed ? (C*)w.w1d[i] : (C*)w.w1[i];
+        a[i].w2 = fp64_of_mixed ? (C*)w.w2d[i] : (C*)w.w2[i];
+        a[i].omega2 = (T)(h->omega * h->omega);
+        a[i].run = nullptr;
+        a[i].count = nullptr;
+    }
+    ApplySys<T>* dev = (ApplySys<T>*)w.sys_x;
+    CK(h, cudaMemcpyAsync(dev, a.data(), nsys * sizeof(ApplySys<T>), cudaMemcpyHostToDevice, s->st));
+    const Plans& pl = f32 ? s->pl32 : s->pl64;
+    double best_ms[6];
+    for (int k = 0; k < 6; ++k) {
+        best[k] = 0;
+        best_ms[k] = 1e300;
+    }
+    for (int var = 0; var <= 3; ++var) {
+        for (int k = 1; k < 6; ++k) s->sched[p][k] = (k == 3 || var < 3) ? var : 0;
+        const Medium m = medium_of(s, f32);
+        cudaError_t e = launch_apply<T>(m, pl, dev, nsys, s->st, &h->nl);   // warm-up
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "lsm_autotune");
+        ktimer_flush(&t);
+        double before[6];
+        for (int k = 0; k < 6; ++k) before[k] = t.ms[6 * p + k];
+        t.on = 1;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_apply<T>(m, pl, dev, nsys, s->st, &h->nl);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        t.on = 0;
+        if (e != cudaSuccess) return cuda_fail(h, e, "lsm_autotune");
+        ktimer_flush(&t);
+        for (int k = 1; k < 6; ++k) {
+            if (var == 3 && k != 3) continue;
+            const double ms = t.ms[6 * p + k] - before[k];
+            if (ms < best_ms[k]) {
+                best_ms[k] = ms;
+                best[k] = var;
+            }
+        }
+    }
+    for (int k = 0; k < 6; ++k) s->sched[p][k] = best[k];
+    return LSM_OK;
+}
+
+extern "C" lsm_status lsm_autotune(lsm_t h, int nsys, int reps, int v64[6], int v32[6]) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_autotune: null handle");
+    if (nsys < 1 || nsys > 64 || reps < 1 || reps > 100)
+        return fail(h, LSM_ERR_ARG, "lsm_autotune: nsys must be in 1..64 and reps in 1..100");
+    Store* s = h->s;
+    lsm_status rc = tune_workspace(h, nsys);
+    if (rc == LSM_OK) rc = timer_events(h);
+    if (rc != LSM_OK) return rc;
+    CK(h, cudaStreamSynchronize(s->st));
+    KTimer& t = s->timer;
+    const int was_on = t.on;
+    t.on = 0;
+    t.used = 0;
+    t.open = 0;
+    const size_t bytes = 3 * (size_t)s->d.N * sizeof(double2);
+    void* buf = nullptr;
+    CK(h, cudaMalloc(&buf, (1 + (size_t)nsys) * bytes));
+    void* u = buf;
+    void* out = (char*)buf + bytes;
+    cudaError_t e = cudaMemsetAsync(u, 0, bytes, s->st);   // FFT time does not depend on the values
+    int best64[6], best32[6] = {0, 0, 0, 0, 0, 0};
+    if (e == cudaSuccess) {
+        rc = tune_one<double>(h, nsys, reps, u, out, best64);
+        if (rc == LSM_OK && s->precision == LSM_MIXED) rc = tune_one<float>(h, nsys, reps, u, out, best32);
+    }
+    cudaStreamSynchronize(s->st);
+    cudaFree(buf);
+    t.on = was_on;
+    t.used = 0;
+    t.open = 0;
+    for (int k = 0; k < 12; ++k) {
+        t.ms[k] = 0.0;
+        t.launches[k] = 0;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "lsm_autotune");
+    if (rc != LSM_OK) return rc;
+    drop_graphs(s->ws);
+    if (v64)
+        for (int k = 0; k < 6; ++k) v64[k] = best64[k];
+    if (v32)
+        for (int k = 0; k < 6; ++k) v32[k] = best32[k];
+    return LSM_OK;
+}
+
 extern "C" lsm_status lsm_dot_c64(lsm_t h, long long n, const void* a, const void* b, double out[2]) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_dot_c64: null handle");
     if (!a || !b || !out || n < 0) return fail(h, LSM_ERR_ARG, "lsm_dot_c64: null pointer or negative length");
@@ -912,12 +1064,8 @@ extern "C" lsm_status lsm_timer_start(lsm_t h, int enable) {
     Store* s = h->s;
     CK(h, cudaStreamSynchronize(s->st));
     KTimer& t = s->timer;
-    if (!t.ev) {
-        t.cap = 4096;
-        t.ev = new cudaEvent_t[2 * t.cap];
-        t.tag = new int[t.cap];
-        for (int i = 0; i < 2 * t.cap; ++i) CK(h, cudaEventCreate(&t.ev[i]));
-    }
+    lsm_status rc = timer_events(h);
+    if (rc != LSM_OK) return rc;
     t.on = enable ? 1 : 0;
     t.used = 0;
     t.open = 0;

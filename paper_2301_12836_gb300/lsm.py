@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_source_moments", "lsm_apply", "lsm_apply_c64",
            "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
-           "lsm_source_gradient", "lsm_time_traces", "lsm_dot_c64", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
+           "lsm_source_gradient", "lsm_time_traces", "lsm_set_schedule", "lsm_get_schedule", "lsm_autotune", "lsm_dot_c64", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
 
@@ -75,6 +75,12 @@ def load(path: str = LIB_PATH):
     lib.lsm_source_moments.restype = i
     lib.lsm_dot_c64.argtypes = [vp, ct.c_longlong, vp, vp, ct.POINTER(d)]
     lib.lsm_dot_c64.restype = i
+    lib.lsm_set_schedule.argtypes = [vp, i, ct.POINTER(i)]
+    lib.lsm_set_schedule.restype = i
+    lib.lsm_get_schedule.argtypes = [vp, i, ct.POINTER(i)]
+    lib.lsm_get_schedule.restype = i
+    lib.lsm_autotune.argtypes = [vp, i, i, ct.POINTER(i), ct.POINTER(i)]
+    lib.lsm_autotune.restype = i
     for name in ("lsm_apply", "lsm_apply_c64", "lsm_adjoint"):
         getattr(lib, name).argtypes = [vp, vp, vp]
         getattr(lib, name).restype = i
@@ -276,6 +282,26 @@ def lsm_time_traces(spectra: torch.Tensor, df, nt, dt, fp, t0, stream: torch.cud
 
 def lsm_launch_count(h: Handle) -> int:
     return int(load().lsm_launch_count(h.ptr))
+
+
+def lsm_set_schedule(h: Handle, precision: int, v) -> None:
+    arr = (ct.c_int * 6)(*[int(x) for x in v])
+    _check(load().lsm_set_schedule(h.ptr, int(precision), arr), h.ptr)
+
+
+def lsm_get_schedule(h: Handle, precision: int):
+    arr = (ct.c_int * 6)()
+    _check(load().lsm_get_schedule(h.ptr, int(precision), arr), h.ptr)
+    return list(arr)
+
+
+def lsm_autotune(h: Handle, nsys: int = 1, reps: int = 2):
+    """Time every FFT schedule variant per stage on batches of nsys systems and keep the fastest;
+    returns (v64, v32)."""
+    a = (ct.c_int * 6)()
+    b = (ct.c_int * 6)()
+    _check(load().lsm_autotune(h.ptr, int(nsys), int(reps), a, b), h.ptr)
+    return list(a), list(b)
 
 
 def lsm_dot_c64(h: Handle, a: torch.Tensor, b: torch.Tensor) -> complex:

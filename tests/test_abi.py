@@ -104,5 +104,8 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lsm_solve(None, None, None, None, None) == lsm.LSM_ERR_ARG
     assert lib.lsm_solve_batched(0, None, None, None, None, None, None) == lsm.LSM_ERR_ARG
     assert lib.lsm_source_moments(None, 1, None, None, None) == lsm.LSM_ERR_ARG
+    assert lib.lsm_set_schedule(None, 0, None) == lsm.LSM_ERR_ARG
+    assert lib.lsm_autotune(None, 1, 1, None, None) == lsm.LSM_ERR_ARG
+    assert lib.lsm_dot_c64(None, 0, None, None, None) == lsm.LSM_ERR_ARG
     lib.lsm_destroy(None)
     assert lib.lsm_launch_count(None) == 0
