@@ -110,14 +110,23 @@ __global__ void __launch_bounds__(NTH) k_stress(Dims d, const T* __restrict__ dC
         const int ix = (int)(idx % d.nx);
         const int iy = (int)((idx / d.nx) % d.ny);
         const int iz = (int)(idx / sxy);
+        // Eq. 18: central differences, one-sided on the first and last node of an axis.  FP64
+        // (arithmetic-bound) takes it without branches: the neighbour offsets collapse to the node
+        // itself at the ends, where the step is h instead of 2h, so all loads issue together;
+        // FP32 (memory-bound) measured faster with the ends as branches.
         auto der = [&](int c, int a) -> C {
             const C* f = u + c * N;
             const int i = a == 0 ? ix : (a == 1 ? iy : iz);
             const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
             const long long s = a == 0 ? 1 : (a == 1 ? (long long)d.nx : sxy);
-            if (i == 0) return cscale(csub(f[idx + s], f[idx]), ih);
-            if (i == n - 1) return cscale(csub(f[idx], f[idx - s]), ih);
-            return cscale(csub(f[idx + s], f[idx - s]), i2h);
+            if constexpr (sizeof(T) == 8) {
+                const long long op = i < n - 1 ? s : 0, om = i > 0 ? s : 0;
+                return cscale(csub(f[idx + op], f[idx - om]), (op != 0 && om != 0) ? i2h : ih);
+            } else {
+                if (i == 0) return cscale(csub(f[idx + s], f[idx]), ih);
+                if (i == n - 1) return cscale(csub(f[idx], f[idx - s]), ih);
+                return cscale(csub(f[idx + s], f[idx - s]), i2h);
+            }
         };
         C e[6];
         e[0] = der(0, 0);
@@ -255,7 +264,7 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const ty
 // memory asynchronously, once for all consecutive systems that share the spectrum (the sources
 // of one frequency), while the first of them runs its forward FFT.
 template <typename T, bool CONJ, int A, int B, int TX>
-__global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 4 ? 3 : 1) k4_fftz_green(
+__global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 4 ? 2 : 1) k4_fftz_green(
     Dims d, const typename cplx_of<T>::type* __restrict__ tw, const ApplySys<T>* __restrict__ sys, int nsys, int in_count,
     int in_off, int out_count, int out_off, int src_sel, int dst_sel) {
     typedef typename cplx_of<T>::type C;
@@ -649,16 +658,16 @@ __global__ void __launch_bounds__(NTH) k_divq(Dims d, const T* __restrict__ drho
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             // the neighbours p +- e_k are model nodes when the other two coordinates are inside
-            // and p_k + 1 (resp. p_k - 1) is inside along k
+            // and p_k + 1 (resp. p_k - 1) is inside along k; loads are predicated, not branched
             const bool other = (k == 0 ? (in1 && in2) : (k == 1 ? (in0 && in2) : (in0 && in1)));
-            if (!other) continue;
-            const bool hi = p[k] + 1 >= 0 && p[k] + 1 < nn[k];
-            const bool lo = p[k] - 1 >= 0 && p[k] - 1 < nn[k];
+            const bool hi = other && p[k] + 1 >= 0 && p[k] + 1 < nn[k];
+            const bool lo = other && p[k] - 1 >= 0 && p[k] - 1 < nn[k];
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const C* sJ = sig + (long long)t2v(j, k) * N + base;
-                if (hi) qj[j] = cadd(qj[j], sJ[st[k]]);
-                if (lo) qj[j] = csub(qj[j], sJ[-st[k]]);
+                const C vh = hi ? sJ[st[k]] : czero<C>();
+                const C vl = lo ? sJ[-st[k]] : czero<C>();
+                qj[j] = cadd(qj[j], csub(vh, vl));
             }
         }
 #pragma unroll
@@ -745,15 +754,33 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftx_out(Dims d,
         const int i = tid + k * NTHR;
         s[(i % L) * LD + i / L] = v[k];
     }
+    // FP32: u for the epilogue is fetched now, so its latency overlaps the transform (nx = L / 2);
+    // FP64 is bound by its arithmetic, and the registers cost it occupancy, so it reads u at the end
+    constexpr int NX = L / 2, PO = NL * NX / NTHR;
+    constexpr bool PRE = sizeof(T) == 4;
+    const C* __restrict__ uin = S.u;
+    C uo[PRE ? PO : 1];
+    if constexpr (PRE) {
+#pragma unroll
+        for (int k = 0; k < PO; ++k) {
+            const int i = tid + k * NTHR;
+            const int x = i % NX, l = i / NX;
+            const int c = l / ROWS, y = y0 + l % ROWS;
+            uo[k] = (y < d.ny) ? uin[(((long long)c * d.nz + z) * d.ny + y) * NX + x] : czero<C>();
+        }
+    }
     __syncthreads();
     fft4_smem<A, B, 1>(s, NL, LD, tw, tid);
-    const int nx = d.nx;
-    for (int i = tid; i < NL * nx; i += NTHR) {
-        const int x = i % nx, l = i / nx;
+    C* __restrict__ out = S.out;
+#pragma unroll
+    for (int k = 0; k < PO; ++k) {
+        const int i = tid + k * NTHR;
+        const int x = i % NX, l = i / NX;
         const int c = l / ROWS, y = y0 + l % ROWS;
         if (y < d.ny) {
-            const long long idx = (((long long)c * d.nz + z) * d.ny + y) * nx + x;
-            S.out[idx] = csub(S.u[idx], s[(x + xoff) * LD + l]);
+            const long long idx = (((long long)c * d.nz + z) * d.ny + y) * NX + x;
+            const C uv = PRE ? uo[PRE ? k : 0] : uin[idx];
+            out[idx] = csub(uv, s[(x + xoff) * LD + l]);
         }
     }
     if (S.count && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(S.count, 1ull);
