@@ -254,7 +254,9 @@ long long lsm_launch_count(lsm_t h);
 
 /*
  * FFT schedules (no counterpart in the paper).  Each apply stage can run one of
- * a few kernel variants: v[0] (strain + contraction) is always 0; v[1] forward
+ * a few kernel variants: v[0] strain + contraction: 0 = stress kernel, then the
+ * divergence with the forward x pass, 1 = contraction and divergence fused in
+ * one z-marching kernel (no stress round trip through memory); v[1] forward
  * x pass, v[2] forward y pass, v[4] inverse y pass, v[5] inverse x pass and
  * epilogue: 0 = compile-time two-step FFT where the line length allows it
  * (16..256), 1 = runtime mixed-radix Stockham engine, 2 = the same with half

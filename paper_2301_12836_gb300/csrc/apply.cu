@@ -96,6 +96,55 @@ __device__ __forceinline__ void ghat_at(const C* __restrict__ g, const Dims& d, 
 // ---------------------------------------------------------------------------------------------
 // strain + contraction
 // ---------------------------------------------------------------------------------------------
+// Contrast stress at one model node (Eqs. 18 and 11): Voigt strain from central differences
+// (one-sided on the first and last node of an axis), contracted with the 21 contrast planes.
+// FP64 (arithmetic-bound) takes the differences without branches: the neighbour offsets collapse
+// to the node itself at the ends, where the step is h instead of 2h, so all loads issue together;
+// FP32 (memory-bound) measured faster with the ends as branches.  Same arithmetic either way.
+template <typename T>
+__device__ __forceinline__ void stress_at(const Dims& d, const T* __restrict__ dC, const typename cplx_of<T>::type* __restrict__ u,
+                                          long long idx, int ix, int iy, int iz, typename cplx_of<T>::type (&sg)[6]) {
+    typedef typename cplx_of<T>::type C;
+    const long long N = d.N;
+    const long long sxy = (long long)d.nx * d.ny;
+    const T ih = (T)(1.0 / d.h), i2h = (T)(0.5 / d.h);
+    auto der = [&](int c, int a) -> C {
+        const C* f = u + c * N;
+        const int i = a == 0 ? ix : (a == 1 ? iy : iz);
+        const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
+        const long long s = a == 0 ? 1 : (a == 1 ? (long long)d.nx : sxy);
+        if constexpr (sizeof(T) == 8) {
+            const long long op = i < n - 1 ? s : 0, om = i > 0 ? s : 0;
+            return cscale(csub(f[idx + op], f[idx - om]), (op != 0 && om != 0) ? i2h : ih);
+        } else {
+            if (i == 0) return cscale(csub(f[idx + s], f[idx]), ih);
+            if (i == n - 1) return cscale(csub(f[idx], f[idx - s]), ih);
+            return cscale(csub(f[idx + s], f[idx - s]), i2h);
+        }
+    };
+    C e[6];
+    e[0] = der(0, 0);
+    e[1] = der(1, 1);
+    e[2] = der(2, 2);
+    e[3] = cadd(der(1, 2), der(2, 1));
+    e[4] = cadd(der(0, 2), der(2, 0));
+    e[5] = cadd(der(0, 1), der(1, 0));
+    T c21[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) c21[k] = __ldg(&dC[k * N + idx]);
+#pragma unroll
+    for (int J = 0; J < 6; ++J) {
+        C s = czero<C>();
+#pragma unroll
+        for (int K = 0; K < 6; ++K) {
+            const T c = c21[p21(J, K)];
+            s.x += c * e[K].x;
+            s.y += c * e[K].y;
+        }
+        sg[J] = s;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NTH) k_stress(Dims d, const T* __restrict__ dC, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
@@ -104,51 +153,109 @@ __global__ void __launch_bounds__(NTH) k_stress(Dims d, const T* __restrict__ dC
     const C* __restrict__ u = S.u;
     C* __restrict__ sig = S.w1;
     const long long N = d.N;
-    const T ih = (T)(1.0 / d.h), i2h = (T)(0.5 / d.h);
     const long long sxy = (long long)d.nx * d.ny;
     for (long long idx = (long long)blockIdx.x * NTH + threadIdx.x; idx < N; idx += (long long)gridDim.x * NTH) {
         const int ix = (int)(idx % d.nx);
         const int iy = (int)((idx / d.nx) % d.ny);
         const int iz = (int)(idx / sxy);
-        // Eq. 18: central differences, one-sided on the first and last node of an axis.  FP64
-        // (arithmetic-bound) takes it without branches: the neighbour offsets collapse to the node
-        // itself at the ends, where the step is h instead of 2h, so all loads issue together;
-        // FP32 (memory-bound) measured faster with the ends as branches.
-        auto der = [&](int c, int a) -> C {
-            const C* f = u + c * N;
-            const int i = a == 0 ? ix : (a == 1 ? iy : iz);
-            const int n = a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
-            const long long s = a == 0 ? 1 : (a == 1 ? (long long)d.nx : sxy);
-            if constexpr (sizeof(T) == 8) {
-                const long long op = i < n - 1 ? s : 0, om = i > 0 ? s : 0;
-                return cscale(csub(f[idx + op], f[idx - om]), (op != 0 && om != 0) ? i2h : ih);
+        C sg[6];
+        stress_at<T>(d, dC, u, idx, ix, iy, iz, sg);
+#pragma unroll
+        for (int J = 0; J < 6; ++J) sig[J * N + idx] = sg[J];
+    }
+}
+
+// Contrast contraction fused with the divergence (Eqs. 18, 11, 8): q on the extended nodes
+// [-1, n]^3, [3][ez][ey][ex] in w2, with no stress round trip through memory.  A block owns a
+// TX x TY tile of extended (x, y) columns and marches through ZC extended z planes
+// (blockIdx.z = chunk + chunks * system); the stress of three consecutive planes (the tile plus a
+// one-node x/y halo, zero off the model) sits in a shared-memory ring, each plane computed once
+// per tile and chunk (x/y halo nodes by both neighbouring tiles, the two planes before a chunk
+// by both neighbouring chunks).  The arithmetic per q entry is that of k_stress + k_divq, in the
+// same order.
+template <typename T, int TX, int TY, int ZC>
+__global__ void __launch_bounds__(TX * TY) k_sdq(Dims d, const T* __restrict__ dC, const T* __restrict__ drho,
+                                                 const ApplySys<T>* __restrict__ sys) {
+    typedef typename cplx_of<T>::type C;
+    constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY, NT = TX * TY;
+    extern __shared__ unsigned char smem_raw[];
+    C* ring = reinterpret_cast<C*>(smem_raw);   // [3 planes][6 comps][HP]
+    const int chunks = (d.ez + ZC - 1) / ZC;
+    const int chunk = blockIdx.z % chunks;
+    const ApplySys<T> S = sys[blockIdx.z / chunks];
+    if (S.run && !*S.run) return;
+    const C* __restrict__ u = S.u;
+    C* __restrict__ q = S.w2;
+    const long long N = d.N;
+    const long long E = (long long)d.ex * d.ey * d.ez;
+    const long long sxy = (long long)d.nx * d.ny;
+    const T i2h = (T)(0.5 / d.h);
+    const int pz0 = chunk * ZC - 1;                                  // first model plane of the chunk
+    const int pz1 = pz0 + ZC - 1 < d.nz ? pz0 + ZC - 1 : d.nz;       // last
+    const int x0 = blockIdx.x * TX - 1, y0 = blockIdx.y * TY - 1;   // model coordinates of the tile's first column
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int px = x0 + tx, py = y0 + ty;                           // this thread's column, in [-1, n]
+    const bool col_ok = px <= d.nx && py <= d.ny;
+    const bool in_xy = px >= 0 && px < d.nx && py >= 0 && py < d.ny;
+    // stress of model plane z on the halo tile into ring slot (z + 3) % 3
+    auto plane = [&](int z) {
+        C* R = ring + ((z + 3) % 3) * 6 * HP;
+        for (int i = threadIdx.x; i < HP; i += NT) {
+            const int mx = x0 - 1 + i % HX, my = y0 - 1 + i / HX;
+            C sg[6];
+            if (z >= 0 && z < d.nz && mx >= 0 && mx < d.nx && my >= 0 && my < d.ny) {
+                stress_at<T>(d, dC, u, (long long)z * sxy + (long long)my * d.nx + mx, mx, my, z, sg);
             } else {
-                if (i == 0) return cscale(csub(f[idx + s], f[idx]), ih);
-                if (i == n - 1) return cscale(csub(f[idx], f[idx - s]), ih);
-                return cscale(csub(f[idx + s], f[idx - s]), i2h);
+#pragma unroll
+                for (int J = 0; J < 6; ++J) sg[J] = czero<C>();
             }
-        };
-        C e[6];
-        e[0] = der(0, 0);
-        e[1] = der(1, 1);
-        e[2] = der(2, 2);
-        e[3] = cadd(der(1, 2), der(2, 1));
-        e[4] = cadd(der(0, 2), der(2, 0));
-        e[5] = cadd(der(0, 1), der(1, 0));
-        T c21[21];
 #pragma unroll
-        for (int k = 0; k < 21; ++k) c21[k] = __ldg(&dC[k * N + idx]);
-#pragma unroll
-        for (int J = 0; J < 6; ++J) {
-            C s = czero<C>();
-#pragma unroll
-            for (int K = 0; K < 6; ++K) {
-                const T c = c21[p21(J, K)];
-                s.x += c * e[K].x;
-                s.y += c * e[K].y;
-            }
-            sig[J * N + idx] = s;
+            for (int J = 0; J < 6; ++J) R[J * HP + i] = sg[J];
         }
+    };
+    plane(pz0 - 1);
+    plane(pz0);
+    const int c0 = (ty + 1) * HX + (tx + 1);   // this column in the halo tile
+    for (int pz = pz0; pz <= pz1; ++pz) {
+        plane(pz + 1);
+        __syncthreads();
+        if (col_ok) {
+            const C* Rm = ring + ((pz + 2) % 3) * 6 * HP;   // plane pz - 1
+            const C* Rc = ring + ((pz + 3) % 3) * 6 * HP;   // plane pz
+            const C* Rp = ring + ((pz + 4) % 3) * 6 * HP;   // plane pz + 1
+            C qj[3] = {czero<C>(), czero<C>(), czero<C>()};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int vx = t2v(j, 0);
+                qj[j] = cadd(qj[j], csub(Rc[vx * HP + c0 + 1], Rc[vx * HP + c0 - 1]));
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int vy = t2v(j, 1);
+                qj[j] = cadd(qj[j], csub(Rc[vy * HP + c0 + HX], Rc[vy * HP + c0 - HX]));
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int vz = t2v(j, 2);
+                qj[j] = cadd(qj[j], csub(Rp[vz * HP + c0], Rm[vz * HP + c0]));
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) qj[j] = cscale(qj[j], i2h);
+            if (in_xy && pz >= 0 && pz < d.nz) {
+                const long long base = (long long)pz * sxy + (long long)py * d.nx + px;
+                const T w = S.omega2 * __ldg(&drho[base]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const C uj = u[j * N + base];
+                    qj[j].x += w * uj.x;
+                    qj[j].y += w * uj.y;
+                }
+            }
+            const long long eidx = ((long long)(pz + 1) * d.ey + (py + 1)) * d.ex + (px + 1);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) q[j * E + eidx] = qj[j];
+        }
+        __syncthreads();   // the next plane overwrites the ring slot of plane pz - 1
     }
 }
 
@@ -1355,15 +1462,31 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
     const T* drho = (const T*)m.drho;
     KTimer* tm = m.timer;
     const bool f32 = sizeof(T) == 4;
-    // 1. strain + contraction -> w1 [6][N]
-    ktimer_mark(tm, 0, f32, st, 0);
-    k_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
-    ktimer_mark(tm, 0, f32, st, 1);
-    // 2. contrast source on the extended nodes -> w2 [3][ez][ey][ex]; forward x FFT -> w1 [3][ez][ey][Lx]
-    ktimer_mark(tm, 1, f32, st, 0);
-    k_divq<T><<<dim3(grid_elems((long long)d.ex * d.ey * d.ez), nsys), NTH, 0, st>>>(d, drho, sys);
-    launch_xfwd<T>(d, sys, nsys, pl, st, m.sched[1]);
-    ktimer_mark(tm, 1, f32, st, 1);
+    if (m.sched[0] == 1) {
+        // 1+2. contraction fused with the divergence: q on the extended nodes -> w2 [3][ez][ey][ex]
+        constexpr int TXS = 32, TYS = 8, ZC = 16;
+        typedef typename cplx_of<T>::type C;
+        const size_t sm = (size_t)3 * 6 * (TXS + 2) * (TYS + 2) * sizeof(C);
+        smem_attr((const void*)k_sdq<T, TXS, TYS, ZC>, sm);
+        ktimer_mark(tm, 0, f32, st, 0);
+        k_sdq<T, TXS, TYS, ZC><<<dim3(cdiv(d.ex, TXS), cdiv(d.ey, TYS), cdiv(d.ez, ZC) * nsys), TXS * TYS, sm, st>>>(
+            d, dC, drho, sys);
+        ktimer_mark(tm, 0, f32, st, 1);
+        ktimer_mark(tm, 1, f32, st, 0);
+        launch_xfwd<T>(d, sys, nsys, pl, st, m.sched[1]);
+        ktimer_mark(tm, 1, f32, st, 1);
+        if (nl) *nl -= 1;
+    } else {
+        // 1. strain + contraction -> w1 [6][N]
+        ktimer_mark(tm, 0, f32, st, 0);
+        k_stress<T><<<dim3(grid_elems(d.N), nsys), NTH, 0, st>>>(d, dC, sys);
+        ktimer_mark(tm, 0, f32, st, 1);
+        // 2. contrast source on the extended nodes -> w2 [3][ez][ey][ex]; forward x FFT -> w1 [3][ez][ey][Lx]
+        ktimer_mark(tm, 1, f32, st, 0);
+        k_divq<T><<<dim3(grid_elems((long long)d.ex * d.ey * d.ez), nsys), NTH, 0, st>>>(d, drho, sys);
+        launch_xfwd<T>(d, sys, nsys, pl, st, m.sched[1]);
+        ktimer_mark(tm, 1, f32, st, 1);
+    }
     // 3. forward y FFT: w1 [3][ez][ey][Lx] -> w2 [3][ez][Ly][Lx]
     ktimer_mark(tm, 2, f32, st, 0);
     launch_ypass<T, -1>(d, sys, nsys, pl, d.ez, d.ey, 0, d.Ly, 0, 2, 3, st, 3, m.sched[2]);

@@ -903,7 +903,7 @@ extern "C" lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const voi
 // FFT schedules and the tuner
 // ---------------------------------------------------------------------------------------------
 static bool schedule_ok(const int v[6]) {
-    if (v[0] != 0) return false;
+    if (v[0] != 0 && v[0] != 1) return false;
     for (int k = 1; k < 6; ++k)
         if (v[k] < 0 || v[k] > (k == 3 ? 3 : 2)) return false;
     return true;
@@ -966,13 +966,8 @@ static lsm_status tune_one(lsm_t h, int nsys, int reps, const void* u, void* out
     ApplySys<T>* dev = (ApplySys<T>*)w.sys_x;
     CK(h, cudaMemcpyAsync(dev, a.data(), nsys * sizeof(ApplySys<T>), cudaMemcpyHostToDevice, s->st));
     const Plans& pl = f32 ? s->pl32 : s->pl64;
-    double best_ms[6];
-    for (int k = 0; k < 6; ++k) {
-        best[k] = 0;
-        best_ms[k] = 1e300;
-    }
-    for (int var = 0; var <= 3; ++var) {
-        for (int k = 1; k < 6; ++k) s->sched[p][k] = (k == 3 || var < 3) ? var : 0;
+    // stage times (ms over `reps` batched applies) under the schedule currently set
+    auto measure = [&](double (&ms)[6]) -> lsm_status {
         const Medium m = medium_of(s, f32);
         cudaError_t e = launch_apply<T>(m, pl, dev, nsys, s->st, &h->nl);   // warm-up
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
@@ -986,15 +981,40 @@ static lsm_status tune_one(lsm_t h, int nsys, int reps, const void* u, void* out
         t.on = 0;
         if (e != cudaSuccess) return cuda_fail(h, e, "lsm_autotune");
         ktimer_flush(&t);
+        for (int k = 0; k < 6; ++k) ms[k] = t.ms[6 * p + k] - before[k];
+        return LSM_OK;
+    };
+    double best_ms[6];
+    for (int k = 0; k < 6; ++k) {
+        best[k] = 0;
+        best_ms[k] = 1e300;
+    }
+    // stages 1..5: each variant set on all of them at once, the fastest kept per stage
+    for (int var = 0; var <= 3; ++var) {
+        s->sched[p][0] = 0;
+        for (int k = 1; k < 6; ++k) s->sched[p][k] = (k == 3 || var < 3) ? var : 0;
+        double ms[6];
+        lsm_status rc = measure(ms);
+        if (rc != LSM_OK) return rc;
         for (int k = 1; k < 6; ++k) {
             if (var == 3 && k != 3) continue;
-            const double ms = t.ms[6 * p + k] - before[k];
-            if (ms < best_ms[k]) {
-                best_ms[k] = ms;
+            if (ms[k] < best_ms[k]) {
+                best_ms[k] = ms[k];
                 best[k] = var;
             }
         }
     }
+    // stage 0 (separate stress and divergence, or fused): they also change what stage 1 times
+    double two[2];
+    for (int v0 = 0; v0 <= 1; ++v0) {
+        for (int k = 1; k < 6; ++k) s->sched[p][k] = best[k];
+        s->sched[p][0] = v0;
+        double ms[6];
+        lsm_status rc = measure(ms);
+        if (rc != LSM_OK) return rc;
+        two[v0] = ms[0] + ms[1];
+    }
+    best[0] = two[1] < two[0] ? 1 : 0;
     for (int k = 0; k < 6; ++k) s->sched[p][k] = best[k];
     return LSM_OK;
 }
