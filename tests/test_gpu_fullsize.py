@@ -73,3 +73,47 @@ def test_batched_mixed_solve_128(grf128):
         x = host(xsol[j]).reshape(3, 128, 128, 128)
         Ax = op.apply_at_points(x, med, w, PTS[:3])
         assert np.abs(Ax - _at(bh, PTS[:3])).max() < 1e-5 * np.abs(bh).max()
+
+
+PTS256 = [(255, 130, 128), (77, 200, 12)]   # each costs the oracle ~20 s of direct sums
+
+
+@pytest.mark.slow
+def test_tti256_apply_sampled_and_batched_solve():
+    """The largest workload (256^3, TTI layer, dx 5 m): FP64 and FP32 applies at sampled nodes
+    against the oracle's direct sums, and the workload's 4 sources at one frequency in one
+    batched mixed solve with the residual checked at sampled nodes."""
+    wl = sy.get_workload("tti256_batched")
+    med = wl.medium()
+    n = med.shape
+    w = 2 * np.pi * wl.freqs_hz[9]
+    h = handle(med, w, precision=lsm.LSM_MIXED, tol=1e-6)
+    u = field(n, 256)
+    ud = dev(u).reshape(-1)
+    A64 = torch.empty_like(ud)
+    lsm.lsm_apply(h, ud, A64)
+    u32 = ud.to(torch.complex64)
+    A32 = torch.empty_like(u32)
+    lsm.lsm_apply_c64(h, u32, A32)
+    del ud, u32
+    want = op.apply_at_points(u, med, w, PTS256)
+    a64 = host(A64).reshape(3, *n)
+    a32 = host(A32).reshape(3, *n).astype(np.complex128)
+    del A64, A32
+    got64 = np.array([a64[:, iz, iy, ix] for ix, iy, iz in PTS256])
+    got32 = np.array([a32[:, iz, iy, ix] for ix, iy, iz in PTS256])
+    scale = np.abs(a64).max()
+    assert np.abs(got64 - want).max() < 1e-11 * scale
+    assert np.abs(got32 - want).max() < 2e-5 * scale
+    del a64, a32, u
+    M, xs = wl.sources()
+    bs = [torch.empty(3 * h.N, dtype=torch.complex128, device="cuda") for _ in M]
+    lsm.lsm_source_moments(h, M, xs[0], bs)
+    xsol = [torch.zeros_like(b) for b in bs]
+    code, its, rrs, sts = lsm.lsm_solve_batched([h] * len(M), bs, xsol)
+    assert code == lsm.LSM_OK and max(rrs) <= 1e-6
+    x = host(xsol[2]).reshape(3, *n)
+    bh = host(bs[2]).reshape(3, *n)
+    Ax = op.apply_at_points(x, med, w, PTS256[:1])
+    bw = np.array([bh[:, iz, iy, ix] for ix, iy, iz in PTS256[:1]])
+    assert np.abs(Ax - bw).max() < 1e-5 * np.abs(bh).max()
