@@ -371,7 +371,7 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const ty
 // memory asynchronously, once for all consecutive systems that share the spectrum (the sources
 // of one frequency), while the first of them runs its forward FFT.
 template <typename T, bool CONJ, int A, int B, int TX>
-__global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 4 ? 2 : 1) k4_fftz_green(
+__global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, 2) k4_fftz_green(
     Dims d, const typename cplx_of<T>::type* __restrict__ tw, const ApplySys<T>* __restrict__ sys, int nsys, int in_count,
     int in_off, int out_count, int out_off, int src_sel, int dst_sel) {
     typedef typename cplx_of<T>::type C;
