@@ -39,6 +39,27 @@ def test_apply_h_fp64_parity(n, mode, green):
     assert rel(op.FFTOperator(med, W, mode=mode).apply(u), want) > 1e-6
 
 
+@pytest.mark.parametrize("precision", [lsm.LSM_FP64, lsm.LSM_MIXED])
+def test_apply_h_with_taper_and_paper_green(precision):
+    """Options combine: the sampled-H form with the paper's Green's tensor (A.4 + A.5 and its
+    derivatives A.6-A.11) and an absorbing layer of 3 nodes (Eq. 25)."""
+    med = sy.random_medium((15, 12, 10), h=9.0, seed=87, frac=0.2)
+    h = handle(med, W, precision=precision, green=lsm.LSM_GREEN_PAPER, kernel=H, taper=3)
+    want_op = op.FFTOperator(op.tapered(med, 3), W, mode="paper", form="h")
+    if precision == lsm.LSM_FP64:
+        u = field(med.shape, 88)
+        Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+        lsm.lsm_apply(h, dev(u).reshape(-1), Au)
+        want = want_op.apply(u)
+        assert rel(host(Au).reshape(want.shape), want) < 1e-12
+    else:
+        u = field(med.shape, 88, np.complex64)
+        Au = torch.empty(3 * h.N, dtype=torch.complex64, device="cuda")
+        lsm.lsm_apply_c64(h, dev(u).reshape(-1), Au)
+        want = want_op.apply(u.astype(np.complex128))
+        assert rel(host(Au).reshape(want.shape).astype(np.complex128), want) < 1e-5
+
+
 @pytest.mark.parametrize("n", [(16, 16, 16), (12, 25, 9)])
 def test_apply_h_fp32_parity(n):
     med = sy.random_medium(n, h=8.0, seed=sum(n) + 82, frac=0.2)
