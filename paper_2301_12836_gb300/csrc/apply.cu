@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(NTH) k_strided_raw(FftPlan p, const typename c
 // four-step strided pass: step 1 loads straight from global memory, the last step stores straight
 // to global memory; one shared-memory exchange in between.  Block = TX * TPL threads, line l = lx.
 template <typename T, int DIR, int A, int B, int TX>
-__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_strided(const typename cplx_of<T>::type* __restrict__ tw,
+__global__ void __launch_bounds__(TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 8 ? 4 : 2) k4_strided(const typename cplx_of<T>::type* __restrict__ tw,
                                                                      StridedArgs a, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ unsigned char smem_raw[];
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(NTH) k_divq(Dims d, const T* __restrict__ drho
 // four-step contiguous-rows FFT: NL rows per block, compile-time sizes, loads batched in registers.
 // Row r of src starts at src + r * in_count (placed at in_off), row r of dst at dst + r * out_count.
 template <typename T, int DIR, int A, int B, int NL>
-__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_rows(const typename cplx_of<T>::type* __restrict__ tw,
+__global__ void __launch_bounds__(NL * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 8 ? 3 : 2) k4_rows(const typename cplx_of<T>::type* __restrict__ tw,
                                                                   const ApplySys<T>* __restrict__ sys, int src_sel, int dst_sel,
                                                                   long long nrows, int in_count, int in_off, int out_count,
                                                                   int out_off) {
@@ -835,7 +835,7 @@ __global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_rows(const typen
 
 // four-step inverse x FFT + crop + Au = u - u_s; ROWS rows x 3 components per block; src w2.
 template <typename T, int A, int B, int ROWS>
-__global__ void LSM_FFT_BOUND(T, FourStepFFT<A LSM_COMMA B>) k4_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys,
+__global__ void __launch_bounds__(3 * ROWS * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 8 ? 3 : 2) k4_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys,
                                                                       const typename cplx_of<T>::type* __restrict__ tw,
                                                                       int xoff) {
     typedef typename cplx_of<T>::type C;
