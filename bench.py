@@ -376,19 +376,17 @@ def main():
             for j in range(nsys):
                 lsm.lsm_source(h, M[j], xs[j], out[j])
 
-    def step(s, host_out=None):
+    def step(s, xs_=None):
+        xs_ = x if xs_ is None else xs_
         h = handles[fidx[s]]
         sources(h, b)
         for j in range(nsys):
-            x[j].zero_()
-        code, its, rrs, sts = lsm.lsm_solve_batched([h] * nsys, b, x, check=False)
+            xs_[j].zero_()
+        code, its, rrs, sts = lsm.lsm_solve_batched([h] * nsys, b, xs_, check=False)
         if code != lsm.LSM_OK:
             raise RuntimeError(f"solve failed: {lsm.STATUS_NAMES.get(code)} {sts} relres {rrs}")
         stats["iters"].extend(its)
         stats["relres"].extend(rrs)
-        if host_out is not None:
-            for j in range(nsys):
-                host_out[j].copy_(x[j], non_blocking=True)
 
     for s in range(args.warmup):
         step(s)
@@ -475,14 +473,30 @@ def main():
     if cs:
         line["clocks"] = cs
 
-    # end to end through the C ABI with host buffers: results copied to pinned host memory each step
+    # end to end through the C ABI with host buffers: every step's solutions are copied to pinned
+    # host memory inside the timed region.  Two solution sets alternate, and each set's copy runs
+    # on a copy stream while the next step solves into the other set; a set is reused only after
+    # its copy has finished.
     if not args.no_e2e:
-        host = [torch.empty(N3, dtype=torch.complex128, pin_memory=True) for _ in range(nsys)]
+        host = [[torch.empty(N3, dtype=torch.complex128, pin_memory=True) for _ in range(nsys)] for _ in range(2)]
+        xsets = [x, [torch.zeros_like(v) for v in x]]
+        copy_stream = torch.cuda.Stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
         lsm.lsm_timer_start(base, False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for s in range(args.warmup, steps_total):
-            step(s, host_out=host)
+        for i, s in enumerate(range(args.warmup, steps_total)):
+            k = i % 2
+            cur = torch.cuda.current_stream()
+            cur.wait_event(copied[k])
+            step(s, xsets[k])
+            solved = torch.cuda.Event()
+            solved.record(cur)
+            copy_stream.wait_event(solved)
+            with torch.cuda.stream(copy_stream):
+                for j in range(nsys):
+                    host[k][j].copy_(xsets[k][j], non_blocking=True)
+            copied[k].record(copy_stream)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         _, _, (e64, e32) = lsm.lsm_timer_read(base)
