@@ -362,7 +362,9 @@ __global__ void __launch_bounds__(TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) =
         const int eo = k - out_off;
         if (xin && eo >= 0 && eo < out_count) dst[eo * des] = v;
     };
-    fft4_io<A, B, DIR, false, false, TX>(s, tw, threadIdx.x, ld, st, in_off + in_count);
+    // zero-padding pruning pays in FP32; in FP64 the warp holding both kinds of step-1 DFTs runs
+    // both and sets the pace at every barrier
+    fft4_io<A, B, DIR, false, false, TX>(s, tw, threadIdx.x, ld, st, sizeof(T) == 8 ? A * B : in_off + in_count);
 }
 
 // four-step z pass with the Green multiply.  Block = 3 TX * TPL threads; line l = c * TX + lx.
@@ -825,7 +827,7 @@ __global__ void __launch_bounds__(NL * FourStep<A LSM_COMMA B>::TPL, sizeof(T) =
         s[(i % L) * LD + i / L] = v[k];
     }
     __syncthreads();
-    fft4_smem<A, B, DIR>(s, NL, LD, tw, tid, in_off + in_count);
+    fft4_smem<A, B, DIR>(s, NL, LD, tw, tid, sizeof(T) == 8 ? A * B : in_off + in_count);   // as in k4_strided
     for (int i = tid; i < NL * out_count; i += NTHR) {
         const int e = i % out_count, l = i / out_count;
         const long long row = r0 + l;
