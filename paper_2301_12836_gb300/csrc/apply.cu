@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) =
         const int eo = k - out_off;
         if (xin && eo >= 0 && eo < out_count) dst[eo * des] = v;
     };
-    // zero-padding pruning pays in FP32; in FP64 the warp holding both kinds of step-1 DFTs runs
-    // both and sets the pace at every barrier
-    fft4_io<A, B, DIR, false, false, TX>(s, tw, threadIdx.x, ld, st, sizeof(T) == 8 ? A * B : in_off + in_count);
+    // zero padding (forward) and cropping (inverse) pruned: at most A/2 + 1 nonzero step-1 inputs,
+    // at most B/2 + 1 wanted step-2 outputs per DFT (the launcher checks the line's extents)
+    fft4_io<A, B, DIR, false, false, TX, (DIR < 0 ? A / 2 + 1 : A), (DIR > 0 ? B / 2 + 1 : B)>(s, tw, threadIdx.x, ld, st);
 }
 
 // four-step z pass with the Green multiply.  Block = 3 TX * TPL threads; line l = c * TX + lx.
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, 2) k4_f
             return (xin && es >= 0 && es < in_count) ? src[es * plane] : czero<C>();
         };
         auto st_s = [&](int l, int k, C v) { s[k * NL + l] = v; };
-        fft4_io<A, B, -1, false, true, NL>(s, tw, threadIdx.x, ld_g, st_s);
+        fft4_io<A, B, -1, false, true, NL, A / 2 + 1, B>(s, tw, threadIdx.x, ld_g, st_s);
         if (fresh) {
             cp_async_wait_all();
             __syncthreads();
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, 2) k4_f
             const int eo = k - out_off;
             if (xin && eo >= 0 && eo < out_count) dst[eo * plane] = v;
         };
-        fft4_io<A, B, 1, true, false, NL>(s, tw, threadIdx.x, ld_s, st_g);
+        fft4_io<A, B, 1, true, false, NL, A, B / 2 + 1>(s, tw, threadIdx.x, ld_s, st_g);
         __syncthreads();  // the next system's forward step writes s
     }
 }
@@ -530,7 +530,6 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
         // twiddle indices) is recomputed per system instead of held in registers across systems
         int q;
         asm volatile("mov.u32 %0, %1;" : "=r"(q) : "r"(q0));
-        const bool half = q + A * (A / 2) >= nin;   // step-1 inputs a >= A/2 lie in the zero padding
         const ApplySys<float> S = sys[si];
         const int sn = next_running(si + 1);
         cp_async_wait_all();
@@ -557,21 +556,13 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
         for (int c = 0; c < 3; ++c) {
             C v[A];
             const C* xc = sX + c * nin * TX + lx;
-            if (half) {
+            // at most A/2 + 1 nonzero inputs per step-1 DFT (nin <= (A/2 + 1) A, checked at launch)
 #pragma unroll
-                for (int a = 0; a < A / 2; ++a) {
-                    const int e = q + A * a;
-                    v[a] = e < nin ? xc[e * TX] : czero<C>();
-                }
-                dft_reg<A, -1, true>(v);
-            } else {
-#pragma unroll
-                for (int a = 0; a < A; ++a) {
-                    const int e = q + A * a;
-                    v[a] = e < nin ? xc[e * TX] : czero<C>();
-                }
-                dft_reg<A, -1>(v);
+            for (int a = 0; a < A; ++a) {
+                const int e = q + A * a;
+                v[a] = (a < A / 2 + 1 && e < nin) ? xc[e * TX] : czero<C>();
             }
+            dft_reg_p<A, -1, A / 2 + 1, A>(v);
             if (q) {
 #pragma unroll
                 for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], lds_fresh(&sW[q * k1]));
@@ -625,10 +616,10 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
             C v[A];
 #pragma unroll
             for (int t = 0; t < A; ++t) v[t] = sY[t * YS + q * TX + lx];
-            dft_reg<A, 1>(v);
+            dft_reg_p<A, 1, A, A / 2 + 1>(v);   // outputs k < (A/2 + 1) A only (checked at launch)
             C* dc = dst + (long long)c * out_count * plane;
 #pragma unroll
-            for (int k2 = 0; k2 < A; ++k2) {
+            for (int k2 = 0; k2 < A / 2 + 1; ++k2) {
                 const int eo = q + A * k2 - out_off;
                 if (xin && eo >= 0 && eo < out_count) dc[eo * plane] = v[k2];
             }
@@ -827,7 +818,7 @@ __global__ void __launch_bounds__(NL * FourStep<A LSM_COMMA B>::TPL, sizeof(T) =
         s[(i % L) * LD + i / L] = v[k];
     }
     __syncthreads();
-    fft4_smem<A, B, DIR>(s, NL, LD, tw, tid, sizeof(T) == 8 ? A * B : in_off + in_count);   // as in k4_strided
+    fft4_smem<A, B, DIR, (DIR < 0 ? A / 2 + 1 : A), (DIR > 0 ? B / 2 + 1 : B)>(s, NL, LD, tw, tid);   // as in k4_strided
     for (int i = tid; i < NL * out_count; i += NTHR) {
         const int e = i % out_count, l = i / out_count;
         const long long row = r0 + l;
@@ -879,7 +870,7 @@ __global__ void __launch_bounds__(3 * ROWS * FourStep<A LSM_COMMA B>::TPL, sizeo
         }
     }
     __syncthreads();
-    fft4_smem<A, B, 1>(s, NL, LD, tw, tid);
+    fft4_smem<A, B, 1, A, B / 2 + 1>(s, NL, LD, tw, tid);   // outputs x + xoff <= L/2 only
     C* __restrict__ out = S.out;
 #pragma unroll
     for (int k = 0; k < PO; ++k) {
@@ -1133,6 +1124,23 @@ static void smem_attr(const void* k, size_t sm) {
     seen.push_back({k, sm});
 }
 
+// The two-step kernels prune at compile time: a line of length L = A B has at most A/2 + 1
+// nonzero inputs per step-1 DFT and at most B/2 + 1 wanted outputs per step-2 DFT.  True when a
+// line with nonzero inputs below in_end and wanted outputs below out_end fits that; the
+// padded lines here (at most n + 2 = L/2 + 2 of either) always do.
+static bool fourstep_prunable(int L, int in_end, int out_end) {
+    int A, B;
+    switch (L) {
+        case 16: A = 4; B = 4; break;
+        case 32: A = 4; B = 8; break;
+        case 64: A = 8; B = 8; break;
+        case 128: A = 8; B = 16; break;
+        case 256: A = 16; B = 16; break;
+        default: return true;   // generic engine
+    }
+    return in_end <= (A / 2 + 1) * B && out_end <= A * (B / 2 + 1);
+}
+
 // Call fn with the FFT engine for line length L: compile-time four-step for 16..256 unless the
 // schedule variant v asks for the generic engine (v = 1, 2), else generic.
 template <typename Fn>
@@ -1186,6 +1194,7 @@ static void strided_cfg(int L, int ncomp, int& TX, int& threads, size_t& sm, int
 template <typename T>
 static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, cudaStream_t st, int v = 0) {
     typedef typename cplx_of<T>::type C;
+    if (!fourstep_prunable(d.Lx, d.ex, 0)) v = 1;
     const long long nrows = 3LL * d.ez * d.ey;
     with_engine(d.Lx, [&](auto eng) {
         using F = decltype(eng);
@@ -1209,6 +1218,7 @@ static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const P
 template <typename T>
 static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int xoff, cudaStream_t st,
                             int v = 0) {
+    if (!fourstep_prunable(d.Lx, 0, d.nx + xoff)) v = 1;
     typedef typename cplx_of<T>::type C;
     with_engine(d.Lx, [&](auto eng) {
         using F = decltype(eng);
@@ -1234,6 +1244,7 @@ template <typename T, int DIR>
 static void launch_strided(int L, const FftPlan& p, const void* tw, StridedArgs a, int outer, const ApplySys<T>* sys,
                            int nsys, cudaStream_t st, int v = 0) {
     typedef typename cplx_of<T>::type C;
+    if (!fourstep_prunable(L, DIR < 0 ? a.in_off + a.in_count : 0, DIR > 0 ? a.out_off + a.out_count : 0)) v = 1;
     with_engine(L, [&](auto eng) {
         using F = decltype(eng);
         int th;
@@ -1283,6 +1294,7 @@ static void launch_zplain(const Dims& d, const ApplySys<T>* sys, int nsys, const
 template <typename T, bool CONJ>
 static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int in_count, int in_off,
                          int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st, int v = 0) {
+    if (!fourstep_prunable(d.Lz, in_off + in_count, out_off + out_count)) v = 1;
     typedef typename cplx_of<T>::type C;
     with_engine(d.Lz, [&](auto eng) {
         using F = decltype(eng);
@@ -1430,7 +1442,7 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
                 k_rows<T, -1><<<dim3(cdiv(nrows, NL), nsys), NTH, sm, st>>>(pl.px, (const C*)pl.twx, sys, 2, 3, nrows, NL,
                                                                              d.nx, 0, d.Lx, 0);
             }
-        });
+        }, fourstep_prunable(d.Lx, d.nx, 0) ? 0 : 1);
     }
     ktimer_mark(tm, 1, f32, st, 1);
     // 3. forward y FFT: w2 -> w1 [9][nz][Ly][Lx]

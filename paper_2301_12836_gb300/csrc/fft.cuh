@@ -32,6 +32,37 @@ template <int S, typename C> __device__ __forceinline__ void bfly4(C* v) {
     v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
 }
 
+// 4-point DFT whose inputs NZ..3 are zero (NZ = 1..4), computing only its first NO outputs
+// (NO = 1..4); NZ = NO = 4 is bfly4 operation for operation.
+template <int S, int NZ, int NO, typename C> __device__ __forceinline__ void bfly4p(C* v) {
+    static_assert(NZ >= 1 && NZ <= 4 && NO >= 1 && NO <= 4, "bfly4p");
+    if constexpr (NZ == 1) {
+#pragma unroll
+        for (int k = 1; k < NO; ++k) v[k] = v[0];
+        return;
+    } else {
+        C t0, t1, t2, t3;
+        if constexpr (NZ >= 3) {
+            t0 = cadd(v[0], v[2]);
+            t1 = csub(v[0], v[2]);
+        } else {
+            t0 = v[0];
+            t1 = v[0];
+        }
+        if constexpr (NZ == 4) {
+            t2 = cadd(v[1], v[3]);
+            t3 = cmul_si<S>(csub(v[1], v[3]));
+        } else {
+            t2 = v[1];
+            t3 = cmul_si<S>(v[1]);
+        }
+        v[0] = cadd(t0, t2);
+        if constexpr (NO >= 2) v[1] = cadd(t1, t3);
+        if constexpr (NO >= 3) v[2] = csub(t0, t2);
+        if constexpr (NO >= 4) v[3] = csub(t1, t3);
+    }
+}
+
 // 4-point DFT of (v0, v1, 0, 0): the first radix-2 layer has nothing to add.
 template <int S, typename C> __device__ __forceinline__ void bfly4_half(C* v) {
     const C a = v[0], b = v[1], bi = cmul_si<S>(v[1]);

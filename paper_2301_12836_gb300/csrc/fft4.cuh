@@ -54,6 +54,73 @@ template <int S, bool HALF = false, typename C> __device__ __forceinline__ void 
     }
 }
 
+// 16-point DFT whose inputs NZ..15 are zero, computing only its first NO outputs: the zero
+// inputs drop out of the first-layer 4-point DFTs, the unneeded outputs out of the last-layer
+// ones.  NZ = NO = 16 is bfly16 operation for operation.
+template <int S, int NZ, int N2, typename C> __device__ __forceinline__ void b16_first(const C* v, C* y) {
+    constexpr int nz = (NZ - N2 + 3) / 4 < 1 ? 0 : ((NZ - N2 + 3) / 4 > 4 ? 4 : (NZ - N2 + 3) / 4);
+    C a[4];
+    if constexpr (nz == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = czero<C>();
+    } else {
+#pragma unroll
+        for (int k = 0; k < nz; ++k) a[k] = v[N2 + 4 * k];
+        bfly4p<S, nz, 4>(a);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[N2 * 4 + k1] = a[k1];
+}
+template <int S, int NO, int K1, typename C> __device__ __forceinline__ void b16_last(const C* y, C* v) {
+    constexpr int no = (NO - K1 + 3) / 4 < 1 ? 0 : ((NO - K1 + 3) / 4 > 4 ? 4 : (NO - K1 + 3) / 4);
+    if constexpr (no > 0) {
+        C b[4] = {y[K1], y[4 + K1], y[8 + K1], y[12 + K1]};
+        bfly4p<S, 4, no>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < no; ++k2) v[K1 + 4 * k2] = b[k2];
+    }
+}
+template <int S, int NZ, int NO, typename C> __device__ __forceinline__ void bfly16p(C* v) {
+    const double c1 = 0.92387953251128675613;  // cos(pi/8)
+    const double s1 = 0.38268343236508977173;  // sin(pi/8)
+    const double r2 = 0.70710678118654752440;  // 1/sqrt(2)
+    C y[16];
+    b16_first<S, NZ, 0>(v, y);
+    b16_first<S, NZ, 1>(v, y);
+    b16_first<S, NZ, 2>(v, y);
+    b16_first<S, NZ, 3>(v, y);
+    // twiddles W16^(n2 k1), as in bfly16
+    y[5] = cmul_const<S>(y[5], c1, s1);
+    y[6] = cmul_const<S>(y[6], r2, r2);
+    y[7] = cmul_const<S>(y[7], s1, c1);
+    y[9] = cmul_const<S>(y[9], r2, r2);
+    y[10] = cmul_si<S>(y[10]);
+    y[11] = cmul_const<S>(y[11], -r2, r2);
+    y[13] = cmul_const<S>(y[13], s1, c1);
+    y[14] = cmul_const<S>(y[14], -r2, r2);
+    y[15] = cmul_const<S>(y[15], -c1, -s1);
+    b16_last<S, NO, 0>(y, v);
+    b16_last<S, NO, 1>(y, v);
+    b16_last<S, NO, 2>(y, v);
+    b16_last<S, NO, 3>(y, v);
+}
+
+// R-point DFT with inputs NZ..R-1 zero and only the first NO outputs needed.  Pruned forms exist
+// for R = 16 and 4 (and R = 8 with NZ <= 4, R = 2 with NZ = 1); otherwise the full DFT runs.
+template <int R, int S, int NZ, int NO, typename C> __device__ __forceinline__ void dft_reg_p(C* v) {
+    if constexpr (R == 16) {
+        bfly16p<S, NZ, NO>(v);
+    } else if constexpr (R == 4) {
+        bfly4p<S, NZ, NO>(v);
+    } else if constexpr (R == 8) {
+        if constexpr (NZ <= 4) bfly8<S, true>(v);
+        else bfly8<S>(v);
+    } else {
+        if constexpr (NZ == 1) v[1] = v[0];
+        else bfly2<S>(v);
+    }
+}
+
 // R-point DFT in registers; HALF: inputs R/2 .. R-1 are zero.
 template <int R, int S, bool HALF = false, typename C> __device__ __forceinline__ void dft_reg(C* v) {
     if (R == 2) {
@@ -78,10 +145,11 @@ template <int A, int B> struct FourStep {
 
 // In-place FFT (sign S) of NL lines; called by exactly NL * TPL threads, tid < NL * TPL.
 // The caller synchronises before (input written) and gets the result after the final barrier.
-// Elements e >= nin are known to be zero (zero padding): a step-1 DFT whose upper half of
-// inputs lies there skips their loads and its first radix-2 layer.
-template <int A, int B, int S, typename C>
-__device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restrict__ tw, int tid, int nin = A * B) {
+// Zero padding and cropping are pruned at compile time: elements e >= NZ * B of a line are known
+// to be zero (each step-1 DFT has at most NZ nonzero inputs), and only outputs k < NO * A are
+// wanted (each step-2 DFT produces its first NO outputs; the others are left unwritten).
+template <int A, int B, int S, int NZ = A, int NO = B, typename C>
+__device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restrict__ tw, int tid) {
     typedef FourStep<A, B> F;
     const int l = tid % NL;
     const int q = tid / NL;
@@ -89,15 +157,9 @@ __device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restr
 #pragma unroll
     for (int i = 0; i < F::I1; ++i) {
         const int t = q + F::TPL * i;
-        if (t + B * (A / 2) >= nin) {
 #pragma unroll
-            for (int a = 0; a < A / 2; ++a) v[i][a] = s[(t + B * a) * LD + l];
-            dft_reg<A, S, true>(v[i]);
-        } else {
-#pragma unroll
-            for (int a = 0; a < A; ++a) v[i][a] = s[(t + B * a) * LD + l];
-            dft_reg<A, S>(v[i]);
-        }
+        for (int a = 0; a < A; ++a) v[i][a] = a < NZ ? s[(t + B * a) * LD + l] : czero<C>();
+        dft_reg_p<A, S, NZ, A>(v[i]);
         if (t) {
 #pragma unroll
             for (int k1 = 1; k1 < A; ++k1) {
@@ -121,14 +183,14 @@ __device__ __forceinline__ void fft4_smem(C* s, int NL, int LD, const C* __restr
         const int k1 = q + F::TPL * i;
 #pragma unroll
         for (int t = 0; t < B; ++t) w2[i][t] = s[(t * A + k1) * LD + l];
-        dft_reg<B, S>(w2[i]);
+        dft_reg_p<B, S, B, NO>(w2[i]);
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < F::I2; ++i) {
         const int k1 = q + F::TPL * i;
 #pragma unroll
-        for (int k2 = 0; k2 < B; ++k2) s[(k1 + A * k2) * LD + l] = w2[i][k2];
+        for (int k2 = 0; k2 < NO; ++k2) s[(k1 + A * k2) * LD + l] = w2[i][k2];
     }
     __syncthreads();
 }
@@ -154,11 +216,12 @@ __host__ __device__ constexpr int fft4_ystride(int NL) {
 // (IN_SMEM: it reads the buffer s itself, so a barrier separates those reads from the first
 // write into s); st(l, k, v) receives output k of line l (OUT_SMEM: it writes s, so a barrier
 // separates the last reads of s from those writes).  Called by exactly NL * TPL threads.  The
-// intermediate occupies B * fft4_ystride<A, C>(NL) elements of s.  Inputs e >= nin are known to
-// be zero: ld is not called for them, and a step-1 DFT whose upper half of inputs lies there
-// skips its first radix-2 layer.
-template <int A, int B, int S, bool IN_SMEM, bool OUT_SMEM, int NL, typename C, class Ld, class St>
-__device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid, Ld ld, St st, int nin = A * B) {
+// intermediate occupies B * fft4_ystride<A, C>(NL) elements of s.  As in fft4_smem, inputs
+// e >= NZ * B are known to be zero (ld is not called for them) and only outputs k < NO * A are
+// produced (st is not called for the others).
+template <int A, int B, int S, bool IN_SMEM, bool OUT_SMEM, int NL, int NZ = A, int NO = B, typename C, class Ld,
+          class St>
+__device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid, Ld ld, St st) {
     typedef FourStep<A, B> F;
     const int l = tid % NL;
     const int q = tid / NL;
@@ -167,15 +230,13 @@ __device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid,
 #pragma unroll
     for (int i = 0; i < F::I1; ++i) {
         const int t = q + F::TPL * i;
-        if (t + B * (A / 2) >= nin) {
 #pragma unroll
-            for (int a = 0; a < A / 2; ++a) v[i][a] = ld(l, t + B * a);
-            dft_reg<A, S, true>(v[i]);
-        } else {
+        for (int a = 0; a < A; ++a) v[i][a] = a < NZ ? ld(l, t + B * a) : czero<C>();
+    }
 #pragma unroll
-            for (int a = 0; a < A; ++a) v[i][a] = ld(l, t + B * a);
-            dft_reg<A, S>(v[i]);
-        }
+    for (int i = 0; i < F::I1; ++i) {
+        const int t = q + F::TPL * i;
+        dft_reg_p<A, S, NZ, A>(v[i]);
         if (t) {
 #pragma unroll
             for (int k1 = 1; k1 < A; ++k1) {
@@ -199,14 +260,14 @@ __device__ __forceinline__ void fft4_io(C* s, const C* __restrict__ tw, int tid,
         const int k1 = q + F::TPL * i;
 #pragma unroll
         for (int t = 0; t < B; ++t) w2[i][t] = s[t * YS + k1 * NL + l];
-        dft_reg<B, S>(w2[i]);
+        dft_reg_p<B, S, B, NO>(w2[i]);
     }
     if (OUT_SMEM) __syncthreads();
 #pragma unroll
     for (int i = 0; i < F::I2; ++i) {
         const int k1 = q + F::TPL * i;
 #pragma unroll
-        for (int k2 = 0; k2 < B; ++k2) st(l, k1 + A * k2, w2[i][k2]);
+        for (int k2 = 0; k2 < NO; ++k2) st(l, k1 + A * k2, w2[i][k2]);
     }
     if (OUT_SMEM) __syncthreads();
 }

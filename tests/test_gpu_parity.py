@@ -111,7 +111,7 @@ def test_source_on_node_flag():
 # grids spanning several tiles in every pass, ragged tails, odd and non-cubic sizes, minimum size
 # (8, 32, 16) and (64, 8, 12) run every axis through a different FFT engine (four-step 16/64/32,
 # four-step 128 / 16 and generic 24)
-GRIDS = [(2, 2, 2), (5, 3, 4), (20, 18, 15), (16, 16, 16), (12, 25, 9), (8, 32, 16), (64, 8, 12)]
+GRIDS = [(2, 2, 2), (5, 3, 4), (20, 18, 15), (16, 16, 16), (12, 25, 9), (8, 32, 16), (64, 8, 12), (32, 32, 32), (8, 8, 8)]
 
 
 @pytest.mark.parametrize("n", GRIDS)
@@ -127,7 +127,7 @@ def test_apply_fp64_parity(n, mode, green):
     assert rel(u, want) > 1e-3  # the scattered part is resolved
 
 
-@pytest.mark.parametrize("n", [(20, 18, 15), (16, 16, 16), (8, 32, 16), (64, 8, 12)])
+@pytest.mark.parametrize("n", [(20, 18, 15), (16, 16, 16), (8, 32, 16), (64, 8, 12), (32, 32, 32), (8, 8, 8)])
 def test_apply_fp32_parity(n):
     med = sy.random_medium(n, h=8.0, seed=3, frac=0.2)
     h = handle(med, W, precision=lsm.LSM_MIXED)
