@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparator (context only)")
     return ap.parse_args()
 
 
@@ -527,6 +528,32 @@ def main():
                              "iterations_mean": float(np.mean(its)), "relres_max": float(np.max(rrs)),
                              "status": lsm.STATUS_NAMES.get(code), "frequency_hz": freqs[fidx[-1]]}
         del h64
+
+    # context, outside the timed region: cuFFT (through torch.fft) doing only the forward and
+    # inverse 3-D transforms of the three padded components of one FP32 apply (no pruning, no
+    # contraction, no Green multiply), against this library's FFT stages 1-5 of the same apply
+    # (which also form the divergence, skip the padding, multiply by the spectrum and crop)
+    if rank == 0 and not args.no_cufft and args.kernel == "diff":
+        L = [2 * v for v in med.n]
+        buf = torch.zeros((3, L[2], L[1], L[0]), dtype=torch.complex64, device="cuda")
+        for _ in range(2):
+            torch.fft.ifftn(torch.fft.fftn(buf, dim=(-3, -2, -1)), dim=(-3, -2, -1))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            torch.fft.ifftn(torch.fft.fftn(buf, dim=(-3, -2, -1)), dim=(-3, -2, -1))
+        e1.record()
+        torch.cuda.synchronize()
+        del buf
+        ours = sum(st_ms[6 + k] for k in range(1, 6)) / a32 if a32 else None
+        line["cufft_comparator"] = {
+            "cufft_fft_ifft_ms_per_system_apply": round(e0.elapsed_time(e1) / reps, 4),
+            "ours_stages_1_5_ms_per_system_apply": round(ours, 4) if ours else None,
+            "note": "complex64, 3 components, full (2n)^3 transforms vs pruned two-step passes with the "
+                    "divergence, Green multiply and crop fused in; not part of the timed region"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         setup, times = oracle_apply_sample(med, 2 * np.pi * freqs[fidx[0]], reps=1)
