@@ -1199,7 +1199,7 @@ static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const P
     with_engine(d.Lx, [&](auto eng) {
         using F = decltype(eng);
         if constexpr (F::INPLACE) {
-            constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 24 : 12;
+            constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 8 : 12;
             const size_t sm = (size_t)A * B * (NL + 1) * sizeof(C);
             smem_attr((const void*)k4_rows<T, -1, A, B, NL>, sm);
             k4_rows<T, -1, A, B, NL><<<dim3(cdiv(nrows, NL), nsys), NL * F::TPL, sm, st>>>(
@@ -1430,7 +1430,7 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
         with_engine(d.Lx, [&](auto eng) {
             using F = decltype(eng);
             if constexpr (F::INPLACE) {
-                constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 24 : 12;
+                constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 8 : 12;
                 const size_t sm = (size_t)A * B * (NL + 1) * sizeof(C);
                 smem_attr((const void*)k4_rows<T, -1, A, B, NL>, sm);
                 k4_rows<T, -1, A, B, NL><<<dim3(cdiv(nrows, NL), nsys), NL * F::TPL, sm, st>>>(
