@@ -59,11 +59,13 @@ typedef enum {
 enum { LSM_FP64 = 0, LSM_MIXED = 1 };
 enum { LSM_GREEN_EXACT = 0, LSM_GREEN_PAPER = 1 };
 enum { LSM_KERNEL_DIFF = 0, LSM_KERNEL_H = 1 };
+enum { LSM_RESIDUAL_DFLOAT = 0, LSM_RESIDUAL_FP64 = 1 };
 
 typedef struct {
     int precision;     /* LSM_FP64: complex128 throughout.
-                          LSM_MIXED: complex64 FFTs/contractions with an FP64 outer
-                          residual and iterative refinement; FP64 inner products. */
+                          LSM_MIXED: complex64 FFTs/contractions with an outer residual
+                          b - A x of Eq. 22 (see residual) and iterative refinement in
+                          complex128 storage; FP64-accurate inner products. */
     int green;         /* LSM_GREEN_EXACT: full isotropic solution of Eq. 7 (default).
                           LSM_GREEN_PAPER: near field Eq. A.4 + far field Eq. A.5. */
     double tol;        /* target relative residual of Eq. 22 (default 1e-10) */
@@ -90,6 +92,13 @@ typedef struct {
                           density), 24 spectra (18 H, 6 G), about 4x the spectrum memory.  The
                           adjoint calls (lsm_adjoint, lsm_solve_adjoint, lsm_gradient) and
                           lsm_apply_static return LSM_ERR_ARG for it. */
+    int residual;      /* LSM_MIXED with LSM_KERNEL_DIFF: arithmetic of the outer residual's
+                          operator apply.  LSM_RESIDUAL_DFLOAT (default): double-float pairs
+                          (two FP32 words, about 48 significand bits, unit roundoff near
+                          2^-48; see lsm_apply_df) on the FP32 pipe, with the iterate scaled
+                          by a power of two to RMS(b) ~ 1 first; LSM_RESIDUAL_FP64: FP64.
+                          Adjoint solves and LSM_KERNEL_H always use FP64.  Ignored for
+                          LSM_FP64 handles. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */
@@ -167,6 +176,22 @@ lsm_status lsm_apply(lsm_t h, const void *u, void *Au);
  * Only for handles created with LSM_MIXED (else LSM_ERR_ARG).
  */
 lsm_status lsm_apply_c64(lsm_t h, const void *u, void *Au);
+
+/*
+ * The operator of lsm_apply in double-float arithmetic: every real quantity of
+ * the path (field, strain, stress, contrast, spectra, twiddles) is carried as
+ * an unevaluated sum hi + lo of two FP32 numbers; sums use two-sum, products
+ * the exact FMA product error (Dekker 1971).  Normwise relative error a few
+ * times 2^-48 times the FFT depth, far below the tolerances FP32 can certify,
+ * at the FP32 pipe's rate.  FP32's exponent range applies: entries of u and
+ * of the intermediate fields must stay within about 1e-30 .. 1e30 in modulus
+ * (the mixed solver scales its iterate first; this entry point does not).
+ *   u, Au  device complex128, 3 * nz*ny*nx; u != Au.  Au is written as
+ *          complex128 (the pairs are converted in place at the end).
+ * Only for handles created with LSM_MIXED, LSM_KERNEL_DIFF and
+ * LSM_RESIDUAL_DFLOAT (else LSM_ERR_ARG).
+ */
+lsm_status lsm_apply_df(lsm_t h, const void *u, void *Au);
 
 /*
  * Adjoint operator A^H v in FP64 (the transposes of the apply's steps in

@@ -17,6 +17,7 @@
 // one node (index p holds node p - 1) so that it occupies [0, n+2) of the 2n-periodic grid;
 // the result is then read at indices 1..n.  1/P of the inverse FFT is folded into G-hat.
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.h"
@@ -1045,6 +1046,7 @@ __global__ void __launch_bounds__(NTH) k_adj_out(Dims d, const T* __restrict__ d
 // ---------------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------------
+#ifndef LSM_APPLY_DFLOAT_TU
 void apply_ws_elems(const Dims& d, int kernel, long long* w1, long long* w2) {
     if (kernel == 1) {
         // sampled-H form: w1 holds [9][N], then [9][nz][Ly][Lx], then [3][nz][Ly][Lx];
@@ -1068,6 +1070,7 @@ void apply_ws_elems(const Dims& d, int kernel, long long* w1, long long* w2) {
     *w1 = m;
     *w2 = m;
 }
+#endif
 
 static const size_t SMEM_CAP = 96 * 1024;
 
@@ -1143,19 +1146,26 @@ static bool fourstep_prunable(int L, int in_end, int out_end) {
 
 // Call fn with the FFT engine for line length L: compile-time four-step for 16..256 unless the
 // schedule variant v asks for the generic engine (v = 1, 2), else generic.
-template <typename Fn>
+// ONLY256 (the double-float operator): the compile-time engine for L = 256 only, every other length
+// generic, which keeps that translation unit's build short.
+template <bool ONLY256 = false, typename Fn>
 static void with_engine(int L, Fn&& fn, int v = 0) {
-    if (v == 1 || v == 2) {
-        fn(GenericFFT());
-        return;
-    }
-    switch (L) {
-        case 16: fn(FourStepFFT<4, 4>()); break;
-        case 32: fn(FourStepFFT<4, 8>()); break;
-        case 64: fn(FourStepFFT<8, 8>()); break;
-        case 128: fn(FourStepFFT<8, 16>()); break;
-        case 256: fn(FourStepFFT<16, 16>()); break;
-        default: fn(GenericFFT()); break;
+    if constexpr (ONLY256) {
+        if (L == 256 && v != 1 && v != 2) fn(FourStepFFT<16, 16>());
+        else fn(GenericFFT());
+    } else {
+        if (v == 1 || v == 2) {
+            fn(GenericFFT());
+            return;
+        }
+        switch (L) {
+            case 16: fn(FourStepFFT<4, 4>()); break;
+            case 32: fn(FourStepFFT<4, 8>()); break;
+            case 64: fn(FourStepFFT<8, 8>()); break;
+            case 128: fn(FourStepFFT<8, 16>()); break;
+            case 256: fn(FourStepFFT<16, 16>()); break;
+            default: fn(GenericFFT()); break;
+        }
     }
 }
 
@@ -1196,7 +1206,7 @@ static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const P
     typedef typename cplx_of<T>::type C;
     if (!fourstep_prunable(d.Lx, d.ex, 0)) v = 1;
     const long long nrows = 3LL * d.ez * d.ey;
-    with_engine(d.Lx, [&](auto eng) {
+    with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
         using F = decltype(eng);
         if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 8 : 12;
@@ -1220,7 +1230,7 @@ static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, con
                             int v = 0) {
     if (!fourstep_prunable(d.Lx, 0, d.nx + xoff)) v = 1;
     typedef typename cplx_of<T>::type C;
-    with_engine(d.Lx, [&](auto eng) {
+    with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
         using F = decltype(eng);
         if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, ROWS = sizeof(T) == 4 ? 8 : 4;
@@ -1245,7 +1255,7 @@ static void launch_strided(int L, const FftPlan& p, const void* tw, StridedArgs 
                            int nsys, cudaStream_t st, int v = 0) {
     typedef typename cplx_of<T>::type C;
     if (!fourstep_prunable(L, DIR < 0 ? a.in_off + a.in_count : 0, DIR > 0 ? a.out_off + a.out_count : 0)) v = 1;
-    with_engine(L, [&](auto eng) {
+    with_engine<std::is_same<T, dfloat>::value>(L, [&](auto eng) {
         using F = decltype(eng);
         int th;
         size_t sm;
@@ -1296,7 +1306,7 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
                          int out_count, int out_off, int src_sel, int dst_sel, cudaStream_t st, int v = 0) {
     if (!fourstep_prunable(d.Lz, in_off + in_count, out_off + out_count)) v = 1;
     typedef typename cplx_of<T>::type C;
-    with_engine(d.Lz, [&](auto eng) {
+    with_engine<std::is_same<T, dfloat>::value>(d.Lz, [&](auto eng) {
         using F = decltype(eng);
         int TX, th;
         size_t sm;
@@ -1427,7 +1437,7 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
     ktimer_mark(tm, 1, f32, st, 0);
     {
         const long long nrows = 9LL * d.nz * d.ny;
-        with_engine(d.Lx, [&](auto eng) {
+        with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
             using F = decltype(eng);
             if constexpr (F::INPLACE) {
                 constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 8 : 12;
@@ -1470,13 +1480,22 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
 template <typename T>
 cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
                          long long* nl) {
-    if (m.kernel == 1) return launch_apply_h<T>(m, pl, sys, nsys, st, nl);
+    // the double-float operator: difference form, default schedule
+    constexpr bool PAIR = std::is_same<T, dfloat>::value;
+    if constexpr (PAIR) {
+        if (m.kernel == 1) return cudaErrorInvalidValue;
+    } else {
+        if (m.kernel == 1) return launch_apply_h<T>(m, pl, sys, nsys, st, nl);
+    }
     const Dims& d = m.d;
     const T* dC = (const T*)m.dC;
     const T* drho = (const T*)m.drho;
     KTimer* tm = m.timer;
     const bool f32 = sizeof(T) == 4;
-    if (m.sched[0] == 1) {
+    int sched[6];
+    for (int k = 0; k < 6; ++k) sched[k] = PAIR ? 0 : m.sched[k];
+    if (!PAIR && sched[0] == 1) {
+      if constexpr (!PAIR) {
         // 1+2. contraction fused with the divergence: q on the extended nodes -> w2 [3][ez][ey][ex]
         constexpr int TXS = 32, TYS = 8, ZC = 16;
         typedef typename cplx_of<T>::type C;
@@ -1487,9 +1506,10 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
             d, dC, drho, sys);
         ktimer_mark(tm, 0, f32, st, 1);
         ktimer_mark(tm, 1, f32, st, 0);
-        launch_xfwd<T>(d, sys, nsys, pl, st, m.sched[1]);
+        launch_xfwd<T>(d, sys, nsys, pl, st, sched[1]);
         ktimer_mark(tm, 1, f32, st, 1);
         if (nl) *nl -= 1;
+      }
     } else {
         // 1. strain + contraction -> w1 [6][N]
         ktimer_mark(tm, 0, f32, st, 0);
@@ -1498,24 +1518,24 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
         // 2. contrast source on the extended nodes -> w2 [3][ez][ey][ex]; forward x FFT -> w1 [3][ez][ey][Lx]
         ktimer_mark(tm, 1, f32, st, 0);
         k_divq<T><<<dim3(grid_elems((long long)d.ex * d.ey * d.ez), nsys), NTH, 0, st>>>(d, drho, sys);
-        launch_xfwd<T>(d, sys, nsys, pl, st, m.sched[1]);
+        launch_xfwd<T>(d, sys, nsys, pl, st, sched[1]);
         ktimer_mark(tm, 1, f32, st, 1);
     }
     // 3. forward y FFT: w1 [3][ez][ey][Lx] -> w2 [3][ez][Ly][Lx]
     ktimer_mark(tm, 2, f32, st, 0);
-    launch_ypass<T, -1>(d, sys, nsys, pl, d.ez, d.ey, 0, d.Ly, 0, 2, 3, st, 3, m.sched[2]);
+    launch_ypass<T, -1>(d, sys, nsys, pl, d.ez, d.ey, 0, d.Ly, 0, 2, 3, st, 3, sched[2]);
     ktimer_mark(tm, 2, f32, st, 1);
     // 4. z FFT, Green multiply, inverse z FFT, crop: w2 [3][ez][Ly][Lx] -> w1 [3][nz][Ly][Lx]
     ktimer_mark(tm, 3, f32, st, 0);
-    launch_zpass<T, false>(d, sys, nsys, pl, d.ez, 0, d.nz, 1, 3, 2, st, m.sched[3]);
+    launch_zpass<T, false>(d, sys, nsys, pl, d.ez, 0, d.nz, 1, 3, 2, st, sched[3]);
     ktimer_mark(tm, 3, f32, st, 1);
     // 5. inverse y FFT + crop: w1 [3][nz][Ly][Lx] -> w2 [3][nz][ny][Lx]
     ktimer_mark(tm, 4, f32, st, 0);
-    launch_ypass<T, 1>(d, sys, nsys, pl, d.nz, d.Ly, 0, d.ny, 1, 2, 3, st, 3, m.sched[4]);
+    launch_ypass<T, 1>(d, sys, nsys, pl, d.nz, d.Ly, 0, d.ny, 1, 2, 3, st, 3, sched[4]);
     ktimer_mark(tm, 4, f32, st, 1);
     // 6. inverse x FFT + crop + Au = u - u_s (reads w2)
     ktimer_mark(tm, 5, f32, st, 0);
-    launch_fftx_out<T>(d, sys, nsys, pl, 1, st, m.sched[5]);
+    launch_fftx_out<T>(d, sys, nsys, pl, 1, st, sched[5]);
     ktimer_mark(tm, 5, f32, st, 1);
     if (nl) *nl += 7;
     return cudaGetLastError();
@@ -1566,6 +1586,7 @@ cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* 
     return cudaGetLastError();
 }
 
+#ifndef LSM_APPLY_DFLOAT_TU
 // Gradient of Re<lam, K_T (Dv dC eps(u) + w^2 Emb drho u)> (discrete adjoint of Eqs. 8, 11):
 // z = K_T^H lam (extended nodes, in w1), tau = Dv^T z; packed entry (I, J) gets
 // Re(conj(tau_I) eps_J) (+ Re(conj(tau_J) eps_I) for I != J), drho gets w^2 Re(sum_j conj(z_j) u_j).
@@ -1746,5 +1767,7 @@ cudaError_t init_kernel_attributes() {
     // dynamic shared-memory limits are raised lazily per kernel (smem_attr)
     return cudaSuccess;
 }
+
+#endif  // LSM_APPLY_DFLOAT_TU
 
 }  // namespace lsm

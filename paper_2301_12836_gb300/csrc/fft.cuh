@@ -15,7 +15,7 @@
 // and writes element (j div Ns) Ns R + (j mod Ns) + r Ns of the other buffer.
 // Forward is dir = -1 (numpy's convention); inverse is dir = +1 and unnormalised.
 #pragma once
-#include "common.cuh"
+#include "dfloat.cuh"
 
 namespace lsm {
 

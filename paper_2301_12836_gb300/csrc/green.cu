@@ -396,6 +396,33 @@ __global__ void k_f2d_c(const float2* __restrict__ in, double2* __restrict__ out
         out[i] = make_double2((double)in[i].x, (double)in[i].y);
 }
 
+// double -> double-float: hi = fl32(v), lo = fl32(v - hi); |lo| <= ulp(hi) / 2
+__global__ void k_d2df(const double* __restrict__ in, dfloat* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = in[i];
+        const float h = __double2float_rn(v);
+        out[i] = dfloat(h, __double2float_rn(v - (double)h));
+    }
+}
+// double-float -> double in place (hi + lo rounded once to FP64)
+__global__ void k_df2d(double* buf, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = reinterpret_cast<const float2*>(buf)[i];
+        buf[i] = (double)v.x + (double)v.y;
+    }
+}
+
+cudaError_t launch_d2df(const double* in, dfloat* out, long long n, cudaStream_t st, long long* nl) {
+    k_d2df<<<gsz(n), 256, 0, st>>>(in, out, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+cudaError_t launch_df2d_inplace(void* buf, long long n, cudaStream_t st, long long* nl) {
+    k_df2d<<<gsz(n), 256, 0, st>>>((double*)buf, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t st, long long* nl) {
     k_d2f<<<gsz(n), 256, 0, st>>>(in, out, n);
     if (nl) *nl += 1;

@@ -1,7 +1,7 @@
 // kernels.h - host-side launchers of the CUDA kernels (internal to the library).
 #pragma once
 #include <cuda_runtime.h>
-#include "common.cuh"
+#include "dfloat.cuh"
 
 namespace lsm {
 
@@ -94,7 +94,10 @@ cudaError_t launch_taper(const Dims& d, int width, double* dC, double* drho, cud
 cudaError_t launch_time_traces(int nf, double df, int ntr, const double2* U, int nt, double dt, double fp, double t0,
                                double* out, cudaStream_t st);
 
-// Precision converters.
+// Precision converters.  d2df: n reals to double-float pairs; df2d_inplace: n double-float pairs
+// to doubles in the same memory (8 bytes each).
+cudaError_t launch_d2df(const double* in, dfloat* out, long long n, cudaStream_t st, long long* nlaunch);
+cudaError_t launch_df2d_inplace(void* buf, long long n, cudaStream_t st, long long* nlaunch);
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t st, long long* nlaunch);
 cudaError_t launch_f2d_c(const float2* in, double2* out, long long n, cudaStream_t st, long long* nlaunch);
 

@@ -44,6 +44,8 @@ struct SolverWS {
     std::vector<void*> kry;    // KRY Krylov vectors per system (inner precision)
     std::vector<void*> w1, w2; // inner-precision apply workspaces
     std::vector<double2*> w1d, w2d, ax64;
+    std::vector<dfcplx*> xdf;  // double-float copies of the iterates (pair residual applies)
+    ApplySys<dfloat>* sysdf = nullptr;
     // captured BiCGSTAB iterations, one per (precision, direction); valid while block is
     struct Graph {
         cudaGraphExec_t exec = nullptr;
@@ -75,9 +77,16 @@ struct Store {
     double* drho64 = nullptr;
     float* dC32 = nullptr;
     float* drho32 = nullptr;
-    Plans pl64, pl32;
+    Plans pl64, pl32, pldf;
     double2* tw64 = nullptr;
     float2* tw32 = nullptr;
+    // double-float copies for the mixed refinement residual (LSM_RESIDUAL_DFLOAT)
+    bool pair = false;
+    dfloat* dCdf = nullptr;
+    dfloat* drhodf = nullptr;
+    dfcplx* twdf = nullptr;
+    dfcplx* udf = nullptr;           // lsm_apply_df input copy
+    ApplySys<dfloat>* adf = nullptr;
     // single-apply workspaces and argument slots
     double2 *w1_64 = nullptr, *w2_64 = nullptr;
     float2 *w1_32 = nullptr, *w2_32 = nullptr;
@@ -100,6 +109,7 @@ struct lsm_ctx {
     lsm_opts o;
     double2* ghat64 = nullptr;
     float2* ghat32 = nullptr;
+    dfcplx* ghatdf = nullptr;
     long long nl = 0;
     std::string err;
 };
@@ -159,6 +169,7 @@ void store_release(Store* s) {
     if (--s->refs > 0) return;
     cudaFree(s->dC64); cudaFree(s->drho64); cudaFree(s->dC32); cudaFree(s->drho32);
     cudaFree(s->tw64); cudaFree(s->tw32);
+    cudaFree(s->dCdf); cudaFree(s->drhodf); cudaFree(s->twdf); cudaFree(s->udf); cudaFree(s->adf);
     cudaFree(s->w1_64); cudaFree(s->w2_64); cudaFree(s->w1_32); cudaFree(s->w2_32);
     cudaFree(s->a64); cudaFree(s->a32); cudaFree(s->flag); cudaFree(s->counts); cudaFree(s->grad_scratch);
     if (s->timer.ev) {
@@ -188,6 +199,17 @@ lsm_status ensure_apply_ws(lsm_t h) {
     return LSM_OK;
 }
 
+Medium medium_pair(Store* s) {
+    Medium m;
+    m.d = s->d;
+    m.dC = s->dCdf;
+    m.drho = s->drhodf;
+    m.timer = &s->timer;
+    m.kernel = s->kernel;
+    for (int k = 0; k < 6; ++k) m.sched[k] = 0;
+    return m;
+}
+
 Medium medium_of(Store* s, int prec32) {
     Medium m;
     m.d = s->d;
@@ -212,6 +234,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->taper = 0;
     o->graph = 1;
     o->kernel = LSM_KERNEL_DIFF;
+    o->residual = LSM_RESIDUAL_DFLOAT;
 }
 
 static lsm_status build_spectrum(lsm_t h) {
@@ -233,6 +256,11 @@ static lsm_status build_spectrum(lsm_t h) {
         CK(h, launch_d2f((const double*)h->ghat64, (float*)h->ghat32, 2 * planes * NO, s->st, &h->nl));
         CK(h, cudaStreamSynchronize(s->st));
     }
+    if (s->pair) {
+        CK(h, cudaMalloc(&h->ghatdf, planes * NO * sizeof(dfcplx)));
+        CK(h, launch_d2df((const double*)h->ghat64, (dfloat*)h->ghatdf, 2 * planes * NO, s->st, &h->nl));
+        CK(h, cudaStreamSynchronize(s->st));
+    }
     return LSM_OK;
 }
 
@@ -251,7 +279,8 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     if (opts) o = *opts;
     if ((o.precision != LSM_FP64 && o.precision != LSM_MIXED) || (o.green != LSM_GREEN_EXACT && o.green != LSM_GREEN_PAPER) ||
         !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1 || o.taper < 0 ||
-        (o.graph != 0 && o.graph != 1) || (o.kernel != LSM_KERNEL_DIFF && o.kernel != LSM_KERNEL_H))
+        (o.graph != 0 && o.graph != 1) || (o.kernel != LSM_KERNEL_DIFF && o.kernel != LSM_KERNEL_H) ||
+        (o.residual != LSM_RESIDUAL_DFLOAT && o.residual != LSM_RESIDUAL_FP64))
         return fail(nullptr, LSM_ERR_ARG, "lsm_create: invalid options");
     static bool attrs_done = false;
     if (!attrs_done) {
@@ -267,6 +296,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     s->st = (cudaStream_t)stream;
     s->precision = o.precision;
     s->green = o.green;
+    s->pair = o.precision == LSM_MIXED && o.kernel == LSM_KERNEL_DIFF && o.residual == LSM_RESIDUAL_DFLOAT;
     s->lam = lambda0; s->mu = mu0; s->rho = rho0;
     Dims& d = s->d;
     d.nx = n[0]; d.ny = n[1]; d.nz = n[2];
@@ -294,6 +324,17 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
         CKB(cudaMalloc(&s->tw32, t32.size() * sizeof(float2)));
         CKB(cudaMemcpy(s->tw64, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
         CKB(cudaMemcpy(s->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        if (s->pair) {
+            std::vector<dfcplx> tdf(t64.size());
+            for (size_t i = 0; i < t64.size(); ++i) {
+                tdf[i].x = dfloat(t64[i].x);
+                tdf[i].y = dfloat(t64[i].y);
+            }
+            CKB(cudaMalloc(&s->twdf, tdf.size() * sizeof(dfcplx)));
+            CKB(cudaMemcpy(s->twdf, tdf.data(), tdf.size() * sizeof(dfcplx), cudaMemcpyHostToDevice));
+            s->pldf = s->pl64;
+            s->pldf.twx = s->twdf; s->pldf.twy = s->twdf + d.Lx; s->pldf.twz = s->twdf + d.Lx + d.Ly;
+        }
         s->pl64.twx = s->tw64; s->pl64.twy = s->tw64 + d.Lx; s->pl64.twz = s->tw64 + d.Lx + d.Ly;
         s->pl32.twx = s->tw32; s->pl32.twy = s->tw32 + d.Lx; s->pl32.twz = s->tw32 + d.Lx + d.Ly;
     }
@@ -310,6 +351,13 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
         CKB(cudaMalloc(&s->drho32, d.N * sizeof(float)));
         CKB(launch_d2f(s->dC64, s->dC32, 21 * d.N, s->st, &h->nl));
         CKB(launch_d2f(s->drho64, s->drho32, d.N, s->st, &h->nl));
+    }
+    if (s->pair) {
+        CKB(cudaMalloc(&s->dCdf, 21 * d.N * sizeof(dfloat)));
+        CKB(cudaMalloc(&s->drhodf, d.N * sizeof(dfloat)));
+        CKB(launch_d2df(s->dC64, s->dCdf, 21 * d.N, s->st, &h->nl));
+        CKB(launch_d2df(s->drho64, s->drhodf, d.N, s->st, &h->nl));
+        CKB(cudaMalloc(&s->adf, sizeof(ApplySys<dfloat>)));
     }
     CKB(cudaMalloc(&s->a64, sizeof(ApplySys<double>)));
     CKB(cudaMalloc(&s->a32, sizeof(ApplySys<float>)));
@@ -348,6 +396,7 @@ extern "C" void lsm_destroy(lsm_t h) {
     if (!h) return;
     cudaFree(h->ghat64);
     cudaFree(h->ghat32);
+    cudaFree(h->ghatdf);
     store_release(h->s);
     delete h;
 }
@@ -430,6 +479,33 @@ extern "C" lsm_status lsm_apply_c64(lsm_t h, const void* u, void* Au) {
     return apply_one<float>(h, u, Au, false);
 }
 
+extern "C" lsm_status lsm_apply_df(lsm_t h, const void* u, void* Au) {
+    if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_apply_df: null handle");
+    if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply_df: u and Au must be distinct non-null device buffers");
+    Store* s = h->s;
+    if (!s->pair)
+        return fail(h, LSM_ERR_ARG, "lsm_apply_df: needs a handle created with LSM_MIXED, LSM_KERNEL_DIFF, LSM_RESIDUAL_DFLOAT");
+    lsm_status rc = ensure_apply_ws(h);
+    if (rc != LSM_OK) return rc;
+    const long long n3 = 3 * s->d.N;
+    if (!s->udf) CK(h, cudaMalloc(&s->udf, n3 * sizeof(dfcplx)));
+    CK(h, launch_d2df((const double*)u, (dfloat*)s->udf, 2 * n3, s->st, &h->nl));
+    ApplySys<dfloat> a;
+    a.u = s->udf;
+    a.out = (dfcplx*)Au;
+    a.ghat = h->ghatdf;
+    a.w1 = (dfcplx*)s->w1_64;
+    a.w2 = (dfcplx*)s->w2_64;
+    a.omega2 = dfloat(h->omega * h->omega);
+    a.run = nullptr;
+    a.count = s->counts;
+    CK(h, cudaMemcpyAsync(s->adf, &a, sizeof(a), cudaMemcpyHostToDevice, s->st));
+    cudaError_t e = launch_apply<dfloat>(medium_pair(s), s->pldf, s->adf, 1, s->st, &h->nl);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lsm_apply_df");
+    CK(h, launch_df2d_inplace(Au, 2 * n3, s->st, &h->nl));
+    return LSM_OK;
+}
+
 extern "C" lsm_status lsm_adjoint(lsm_t h, const void* v, void* AHv) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_adjoint: null handle");
     if (!v || !AHv || v == AHv) return fail(h, LSM_ERR_ARG, "lsm_adjoint: v and AHv must be distinct non-null device buffers");
@@ -471,8 +547,9 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     const size_t o_stt = take(nsys * sizeof(ApplySys<double>));
     const size_t o_sx = take(nsys * sizeof(ApplySys<double>));
     const size_t o_s64 = take(nsys * sizeof(ApplySys<double>));
-    const size_t o_ptr = take(6 * (size_t)nsys * sizeof(void*));
-    std::vector<size_t> o_kry, o_w1, o_w2, o_w1d, o_w2d, o_ax;
+    const size_t o_ptr = take(7 * (size_t)nsys * sizeof(void*));
+    const size_t o_sdf = take(nsys * sizeof(ApplySys<dfloat>));
+    std::vector<size_t> o_kry, o_w1, o_w2, o_w1d, o_w2d, o_ax, o_xdf;
     for (int i = 0; i < nsys; ++i) {
         for (int k = 0; k < KRY; ++k) o_kry.push_back(take(n3 * csz));
         if (mixed) {
@@ -481,6 +558,7 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
             o_w1d.push_back(take(e1 * sizeof(double2)));
             o_w2d.push_back(take(e2 * sizeof(double2)));
             o_ax.push_back(take(n3 * sizeof(double2)));
+            if (s->pair) o_xdf.push_back(take(n3 * sizeof(dfcplx)));
         } else {
             o_w1.push_back(take(e1 * csz));
             o_w2.push_back(take(e2 * csz));
@@ -506,6 +584,7 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     w.sys_x = b + o_sx;
     w.sys64 = (ApplySys<double>*)(b + o_s64);
     w.ptrs = (void**)(b + o_ptr);
+    w.sysdf = (ApplySys<dfloat>*)(b + o_sdf);
     for (int i = 0; i < nsys; ++i) {
         for (int k = 0; k < KRY; ++k) w.kry.push_back(b + o_kry[i * KRY + k]);
         if (mixed) {
@@ -514,6 +593,7 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
             w.w1.push_back(b + o_w1d[i]);
             w.w2.push_back(b + o_w2d[i]);
             w.ax64.push_back((double2*)(b + o_ax[i]));
+            if (s->pair) w.xdf.push_back((dfcplx*)(b + o_xdf[i]));
         } else {
             w.w1.push_back(b + o_w1[i]);
             w.w2.push_back(b + o_w2[i]);
@@ -733,7 +813,10 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
         CK(h0, cudaStreamSynchronize(st));
         for (int i = 0; i < nsys; ++i) rr_out[i] = ms[i].relres;
     } else {
-        // mixed precision: FP64 outer residual + FP32 inner BiCGSTAB on the normalised residual
+        // mixed precision: outer residual in double-float (pair) or FP64 arithmetic, FP64 storage, and
+        // FP32 inner BiCGSTAB on the normalised residual
+        const bool pair = s->pair && !adjoint;
+        std::vector<ApplySys<dfloat>> adf(nsys);
         std::vector<BcgVecs<float>> V(nsys);
         std::vector<ApplySys<float>> sv(nsys), stt(nsys);
         for (int i = 0; i < nsys; ++i) {
@@ -759,13 +842,26 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             d.out = w.ax64[i];
             d.run = &w.ms[i].run;
             a64[i] = d;
+            if (pair) {
+                ApplySys<dfloat> q;
+                q.count = s->counts;
+                q.ghat = hs[i]->ghatdf;
+                q.w1 = (dfcplx*)w.w1d[i];
+                q.w2 = (dfcplx*)w.w2d[i];
+                q.omega2 = dfloat(hs[i]->omega * hs[i]->omega);
+                q.u = w.xdf[i];
+                q.out = (dfcplx*)w.ax64[i];   // A x as pairs, read back by the pair residual
+                q.run = &w.ms[i].run;
+                adf[i] = q;
+            }
         }
+        if (pair) CK(h0, cudaMemcpyAsync(w.sysdf, adf.data(), nsys * sizeof(adf[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.vecs, V.data(), nsys * sizeof(V[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys_v, sv.data(), nsys * sizeof(sv[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys_t, stt.data(), nsys * sizeof(stt[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys64, a64.data(), nsys * sizeof(a64[0]), cudaMemcpyHostToDevice, st));
         void** P = w.ptrs;
-        std::vector<void*> hp(6 * nsys);
+        std::vector<void*> hp(7 * nsys, nullptr);
         for (int i = 0; i < nsys; ++i) {
             hp[i] = const_cast<void*>(b[i]);
             hp[nsys + i] = w.ax64[i];
@@ -773,8 +869,9 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             hp[3 * nsys + i] = w.kry[i * KRY + 7];  // r32 (inner b)
             hp[4 * nsys + i] = x[i];
             hp[5 * nsys + i] = w.kry[i * KRY + 0];  // d32
+            if (pair) hp[6 * nsys + i] = w.xdf[i];
         }
-        CK(h0, cudaMemcpyAsync(P, hp.data(), 6 * nsys * sizeof(void*), cudaMemcpyHostToDevice, st));
+        CK(h0, cudaMemcpyAsync(P, hp.data(), 7 * nsys * sizeof(void*), cudaMemcpyHostToDevice, st));
         for (int i = 0; i < nsys; ++i) ms[i].run = 1;
         CK(h0, cudaMemcpyAsync(w.ms, ms.data(), nsys * sizeof(MixState), cudaMemcpyHostToDevice, st));
         // a zero initial guess needs no FP64 apply: its residual is b
@@ -783,11 +880,18 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
         const int nblk = pt.nblk;
         std::vector<double> itol(nsys, h0->o.inner_tol);
         for (int outer = 0;; ++outer) {
-            cudaError_t e = apply_op<double>(adjoint, m64, s->pl64, w.sys64, nsys, st, &h0->nl);
-            if (e != cudaSuccess) return cuda_fail(h0, e, "FP64 residual apply");
+            cudaError_t e;
+            if (pair) {
+                CK(h0, mix_to_pair((const double2* const*)(P + 4 * nsys), (dfcplx* const*)(P + 6 * nsys), w.ms, n3, nsys, nblk,
+                                   st, &h0->nl));
+                e = launch_apply<dfloat>(medium_pair(s), s->pldf, w.sysdf, nsys, st, &h0->nl);
+            } else {
+                e = apply_op<double>(adjoint, m64, s->pl64, w.sys64, nsys, st, &h0->nl);
+            }
+            if (e != cudaSuccess) return cuda_fail(h0, e, "residual apply");
             CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
             CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms,
-                                pt, n3, nsys, w.n_active, st, &h0->nl));
+                                pt, n3, nsys, w.n_active, st, &h0->nl, pair));
             CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
             CK(h0, cudaStreamSynchronize(st));
             ktimer_flush(&s->timer);
@@ -859,6 +963,10 @@ extern "C" lsm_status lsm_set_contrast(lsm_t h, const double* dC, const double* 
     if (s->precision == LSM_MIXED) {
         CK(h, launch_d2f(s->dC64, s->dC32, 21 * N, s->st, &h->nl));
         CK(h, launch_d2f(s->drho64, s->drho32, N, s->st, &h->nl));
+    }
+    if (s->pair) {
+        CK(h, launch_d2df(s->dC64, s->dCdf, 21 * N, s->st, &h->nl));
+        CK(h, launch_d2df(s->drho64, s->drhodf, N, s->st, &h->nl));
     }
     return LSM_OK;
 }

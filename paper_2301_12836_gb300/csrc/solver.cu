@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ v
 // ---------------------------------------------------------------------------------------------
 // mixed-precision refinement
 // ---------------------------------------------------------------------------------------------
+template <bool PAIR>
 __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restrict__ b, const double2* const* __restrict__ ax,
                                                  double2* const* __restrict__ r64, MixState* __restrict__ ms, Partials pt,
                                                  long long n, int* n_active) {
@@ -369,9 +370,19 @@ __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restric
     const double2* AX = ax[sys];
     double2* R = r64[sys];
     const int xz = ms[sys].xzero;
+    const double up = PAIR ? ldexp(1.0, ms[sys].pexp) : 1.0;
     double v[2] = {0.0, 0.0};
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const double2 bb = B[i], a = xz ? make_double2(0.0, 0.0) : AX[i];
+        double2 a = make_double2(0.0, 0.0);
+        if (!xz) {
+            if constexpr (PAIR) {
+                const float4 p = reinterpret_cast<const float4*>(AX)[i];
+                a = make_double2(((double)p.x + (double)p.y) * up, ((double)p.z + (double)p.w) * up);
+            } else {
+                a = AX[i];
+            }
+        }
+        const double2 bb = B[i];
         const double2 r = make_double2(bb.x - a.x, bb.y - a.y);
         R[i] = r;
         v[0] += bb.x * bb.x + bb.y * bb.y;
@@ -400,6 +411,7 @@ __global__ void __launch_bounds__(VTH) k_mix_xnorm(const double2* const* __restr
     }
     double tot[1];
     if (grid_sum<1>(v, pt, sys, &ms[sys].counter, tot)) {
+        ms[sys].xnorm2 = tot[0];
         ms[sys].xzero = tot[0] == 0.0 ? 1 : 0;
         ms[sys].run = !ms[sys].xzero;
     }
@@ -415,6 +427,30 @@ __global__ void __launch_bounds__(VTH) k_mix_down(double2* const* __restrict__ r
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const double2 r = R[i];
         D[i] = make_float2((float)(r.x * sc), (float)(r.y * sc));
+    }
+}
+
+__global__ void __launch_bounds__(VTH) k_mix_to_pair(const double2* const* __restrict__ x64, dfcplx* const* __restrict__ xdf,
+                                                     MixState* __restrict__ ms, long long n) {
+    const int sys = blockIdx.y;
+    if (!ms[sys].run) return;
+    // RMS of b (or of the initial x) in [2^(e-1), 2^e): the scaled entries sit near 1, far from the
+    // ends of the FP32 exponent range that the double-float arithmetic shares
+    const double ref = ms[sys].bnorm2 > 0.0 ? ms[sys].bnorm2 : ms[sys].xnorm2;
+    int e = 0;
+    if (ref > 0.0 && isfinite(ref)) frexp(sqrt(ref / (double)n), &e);
+    const double down = ldexp(1.0, -e);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ms[sys].pexp = e;
+    const double2* X = x64[sys];
+    dfcplx* D = xdf[sys];
+    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+        const double2 x = X[i];
+        const double xr = x.x * down, xi = x.y * down;
+        const float hr = __double2float_rn(xr), hi = __double2float_rn(xi);
+        dfcplx v;
+        v.x = dfloat(hr, __double2float_rn(xr - (double)hr));
+        v.y = dfloat(hi, __double2float_rn(xi - (double)hi));
+        D[i] = v;
     }
 }
 
@@ -524,8 +560,9 @@ LSM_INST(double)
 #undef LSM_INST
 
 cudaError_t mix_residual(const double2* const* b, const double2* const* ax, double2* const* r64, MixState* ms, Partials pt,
-                         long long n, int nsys, int* n_active, cudaStream_t s, long long* nl) {
-    k_mix_res<<<dim3(pt.nblk, nsys), VTH, 0, s>>>(b, ax, r64, ms, pt, n, n_active);
+                         long long n, int nsys, int* n_active, cudaStream_t s, long long* nl, bool pair) {
+    if (pair) k_mix_res<true><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(b, ax, r64, ms, pt, n, n_active);
+    else k_mix_res<false><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(b, ax, r64, ms, pt, n, n_active);
     if (nl) *nl += 1;
     return cudaGetLastError();
 }
@@ -538,6 +575,12 @@ cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms
 cudaError_t mix_xnorm(const double2* const* x64, MixState* ms, Partials pt, long long n, int nsys, cudaStream_t s,
                       long long* nl) {
     k_mix_xnorm<<<dim3(pt.nblk, nsys), VTH, 0, s>>>(x64, ms, pt, n);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+cudaError_t mix_to_pair(const double2* const* x64, dfcplx* const* xdf, MixState* ms, long long n, int nsys, int nblk,
+                        cudaStream_t s, long long* nl) {
+    k_mix_to_pair<<<dim3(nblk, nsys), VTH, 0, s>>>(x64, xdf, ms, n);
     if (nl) *nl += 1;
     return cudaGetLastError();
 }

@@ -44,6 +44,8 @@ struct MixState {
     int run;            // FP64 residual apply runs
     int xzero;          // the iterate is exactly zero: the residual is b, no apply needed
     unsigned int counter;
+    double xnorm2;      // ||x||^2 of the initial iterate
+    int pexp;           // double-float residual apply: x entered scaled by 2^-pexp
 };
 
 struct Partials {
@@ -73,7 +75,13 @@ cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long 
 cudaError_t mix_xnorm(const double2* const* x64, MixState* ms, Partials pt, long long n, int nsys, cudaStream_t s,
                       long long* nl);
 cudaError_t mix_residual(const double2* const* b, const double2* const* ax, double2* const* r64, MixState* ms,
-                         Partials pt, long long n, int nsys, int* n_active, cudaStream_t s, long long* nl);
+                         Partials pt, long long n, int nsys, int* n_active, cudaStream_t s, long long* nl,
+                         bool pair = false);
+// x (complex128) -> double-float pairs scaled by the power of two 2^-pexp that brings the RMS of b
+// (of x before b is known) near 1, recorded in ms.pexp; systems with ms.run == 0 are skipped.
+// pair residuals (mix_residual with pair) read A x as double-float pairs and scale back by 2^pexp.
+cudaError_t mix_to_pair(const double2* const* x64, dfcplx* const* xdf, MixState* ms, long long n, int nsys, int nblk,
+                        cudaStream_t s, long long* nl);
 cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms, long long n, int nsys, int nblk,
                      cudaStream_t s, long long* nl);
 cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, long long n, int nsys, int nblk,

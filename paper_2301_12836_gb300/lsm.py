@@ -28,13 +28,14 @@ LSM_MIXED = 1
 LSM_GREEN_EXACT = 0
 LSM_GREEN_PAPER = 1
 LSM_KERNEL_DIFF, LSM_KERNEL_H = 0, 1
+LSM_RESIDUAL_DFLOAT, LSM_RESIDUAL_FP64 = 0, 1
 
 STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR_OOM", -4: "LSM_ERR_BREAKDOWN",
                 -5: "LSM_ERR_NOCONV", -6: "LSM_ERR_TIMEOUT", 1: "LSM_WARN_SOURCE_ON_NODE"}
 
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_source_moments", "lsm_apply", "lsm_apply_c64",
-           "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
+           "lsm_apply_df", "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
            "lsm_source_gradient", "lsm_time_traces", "lsm_set_schedule", "lsm_get_schedule", "lsm_autotune", "lsm_dot_c64", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
@@ -42,7 +43,7 @@ EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", 
 class lsm_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("green", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
                 ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int), ("graph", ct.c_int),
-                ("kernel", ct.c_int)]
+                ("kernel", ct.c_int), ("residual", ct.c_int)]
 
 
 class LSMError(RuntimeError):
@@ -81,7 +82,7 @@ def load(path: str = LIB_PATH):
     lib.lsm_get_schedule.restype = i
     lib.lsm_autotune.argtypes = [vp, i, i, ct.POINTER(i), ct.POINTER(i)]
     lib.lsm_autotune.restype = i
-    for name in ("lsm_apply", "lsm_apply_c64", "lsm_adjoint"):
+    for name in ("lsm_apply", "lsm_apply_c64", "lsm_apply_df", "lsm_adjoint"):
         getattr(lib, name).argtypes = [vp, vp, vp]
         getattr(lib, name).restype = i
     lib.lsm_solve.argtypes = [vp, vp, vp, ct.POINTER(i), ct.POINTER(d)]
@@ -209,6 +210,10 @@ def lsm_apply(h: Handle, u: torch.Tensor, Au: torch.Tensor) -> None:
 
 def lsm_apply_c64(h: Handle, u: torch.Tensor, Au: torch.Tensor) -> None:
     _check(load().lsm_apply_c64(h.ptr, _ptr(u, torch.complex64, 3 * h.N), _ptr(Au, torch.complex64, 3 * h.N)), h.ptr)
+
+
+def lsm_apply_df(h: Handle, u: torch.Tensor, Au: torch.Tensor) -> None:
+    _check(load().lsm_apply_df(h.ptr, _ptr(u, torch.complex128, 3 * h.N), _ptr(Au, torch.complex128, 3 * h.N)), h.ptr)
 
 
 def lsm_adjoint(h: Handle, v: torch.Tensor, AHv: torch.Tensor) -> None:
