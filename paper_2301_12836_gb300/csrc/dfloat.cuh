@@ -29,6 +29,34 @@ template <> struct real_of<dfcplx> { typedef dfloat type; };
 
 __host__ __device__ inline double df_value(dfloat a) { return (double)a.hi + (double)a.lo; }
 
+// v * 2^-e as a pair: hi = v * 2^-e rounded to FP32 (nearest even), lo = the remainder rounded to
+// FP32, the same pair as hi = fl32(w), lo = fl32(w - hi) for w = v * 2^-e, but by integer operations
+// on the FP64 bit pattern and one int -> float conversion (FP64 arithmetic runs at 1/64 of the FP32
+// rate here).  Results below FP32's normal range give +-0 (lo is dropped below 2^-74), results
+// beyond it +-inf; NaN stays NaN.
+__device__ __forceinline__ dfloat df_split(double v, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int E = (int)((b >> 52) & 0x7ff);
+    const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
+    if (E == 0x7ff) return dfloat(__uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u)), 0.f);
+    const int fe = E - 1023 - e + 127;    // biased FP32 exponent of the leading bit
+    if (E == 0 || fe <= 0) return dfloat(__uint_as_float(sign), 0.f);
+    if (fe >= 255) return dfloat(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const unsigned long long sig = frac | (1ull << 52);          // 53-bit significand
+    const unsigned keep = (unsigned)(sig >> 29);                  // its leading 24 bits
+    const unsigned rem = (unsigned)(sig & 0x1FFFFFFFull);         // the 29 below
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+    // a carry out of the 23 stored bits moves into the exponent field, as it should
+    const unsigned hb = ((unsigned)fe << 23) + (keep - 0x800000u) + up;
+    if (hb >= 0x7f800000u) return dfloat(__uint_as_float(sign | 0x7f800000u), 0.f);
+    // remainder rem - up 2^29 (|.| <= 2^28) in units of 2^(fe - 179)
+    const int r = (int)rem - (int)(up << 29);
+    float lo = 0.f;
+    if (fe > 52 && r != 0) lo = __fmul_rn(__int2float_rn(r), __uint_as_float((unsigned)(fe - 52) << 23));
+    return dfloat(__uint_as_float(sign | hb), sign ? -lo : lo);
+}
+
 // s + e = a + b exactly
 __device__ __forceinline__ dfloat df_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);

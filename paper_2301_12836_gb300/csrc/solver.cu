@@ -360,6 +360,11 @@ __global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ v
 // ---------------------------------------------------------------------------------------------
 // mixed-precision refinement
 // ---------------------------------------------------------------------------------------------
+// r = b - A x and the norms of b and r.  PAIR (double-float residual apply, x entered scaled by
+// 2^-pexp): b is split into pairs at the same scale by integer operations, r = b - A x is one
+// double-float subtraction on the FP32 pipe and is stored as pairs (rpair), and the norms sum the
+// squares of the high words in FP32 per thread (relative error ~1e-6, all a convergence test and a
+// normalisation need), totals in FP64.  Otherwise (FP64 apply, or x = 0 so that r = b): FP64.
 template <bool PAIR>
 __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restrict__ b, const double2* const* __restrict__ ax,
                                                  double2* const* __restrict__ r64, MixState* __restrict__ ms, Partials pt,
@@ -370,30 +375,40 @@ __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restric
     const double2* AX = ax[sys];
     double2* R = r64[sys];
     const int xz = ms[sys].xzero;
-    const double up = PAIR ? ldexp(1.0, ms[sys].pexp) : 1.0;
+    const bool pair = PAIR && !xz;
+    const int pexp = ms[sys].pexp;
     double v[2] = {0.0, 0.0};
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        double2 a = make_double2(0.0, 0.0);
-        if (!xz) {
-            if constexpr (PAIR) {
-                const float4 p = reinterpret_cast<const float4*>(AX)[i];
-                a = make_double2(((double)p.x + (double)p.y) * up, ((double)p.z + (double)p.w) * up);
-            } else {
-                a = AX[i];
-            }
+    if (pair) {
+        float sb = 0.f, sr = 0.f;
+        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+            const double2 bb = B[i];
+            const float4 p = reinterpret_cast<const float4*>(AX)[i];
+            const dfloat br = df_split(bb.x, pexp), bi = df_split(bb.y, pexp);
+            const dfloat rr = br - dfloat(p.x, p.y), ri = bi - dfloat(p.z, p.w);
+            reinterpret_cast<float4*>(R)[i] = make_float4(rr.hi, rr.lo, ri.hi, ri.lo);
+            sb = __fmaf_rn(br.hi, br.hi, __fmaf_rn(bi.hi, bi.hi, sb));
+            sr = __fmaf_rn(rr.hi, rr.hi, __fmaf_rn(ri.hi, ri.hi, sr));
         }
-        const double2 bb = B[i];
-        const double2 r = make_double2(bb.x - a.x, bb.y - a.y);
-        R[i] = r;
-        v[0] += bb.x * bb.x + bb.y * bb.y;
-        v[1] += r.x * r.x + r.y * r.y;
+        v[0] = (double)sb;
+        v[1] = (double)sr;
+    } else {
+        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+            const double2 bb = B[i];
+            const double2 a = xz ? make_double2(0.0, 0.0) : AX[i];
+            const double2 r = make_double2(bb.x - a.x, bb.y - a.y);
+            R[i] = r;
+            v[0] += bb.x * bb.x + bb.y * bb.y;
+            v[1] += r.x * r.x + r.y * r.y;
+        }
     }
     double tot[2];
     if (grid_sum<2>(v, pt, sys, &ms[sys].counter, tot)) {
         MixState& M = ms[sys];
-        M.bnorm2 = tot[0];
-        M.rnorm2 = tot[1];
+        const double sc = pair ? ldexp(1.0, 2 * pexp) : 1.0;
+        M.bnorm2 = tot[0] * sc;
+        M.rnorm2 = tot[1] * sc;
         M.relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+        M.rpair = pair ? 1 : 0;
         M.done = (M.relres <= M.tol || tot[1] == 0.0) ? 1 : 0;
         M.run = !M.done;
         if (!M.done) atomicAdd(n_active, 1);
@@ -424,6 +439,16 @@ __global__ void __launch_bounds__(VTH) k_mix_down(double2* const* __restrict__ r
     const double sc = 1.0 / sqrt(ms[sys].rnorm2);
     const double2* R = r64[sys];
     float2* D = r32[sys];
+    if (ms[sys].rpair) {
+        // pairs at scale 2^-pexp: the high word times 2^pexp / ||r|| in FP32 (the low word is
+        // below the FP32 rounding of the result)
+        const float s32 = (float)(ldexp(1.0, ms[sys].pexp) * sc);
+        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
+            const float4 p = reinterpret_cast<const float4*>(R)[i];
+            D[i] = make_float2(__fmul_rn(p.x, s32), __fmul_rn(p.z, s32));
+        }
+        return;
+    }
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const double2 r = R[i];
         D[i] = make_float2((float)(r.x * sc), (float)(r.y * sc));
@@ -439,17 +464,14 @@ __global__ void __launch_bounds__(VTH) k_mix_to_pair(const double2* const* __res
     const double ref = ms[sys].bnorm2 > 0.0 ? ms[sys].bnorm2 : ms[sys].xnorm2;
     int e = 0;
     if (ref > 0.0 && isfinite(ref)) frexp(sqrt(ref / (double)n), &e);
-    const double down = ldexp(1.0, -e);
     if (blockIdx.x == 0 && threadIdx.x == 0) ms[sys].pexp = e;
     const double2* X = x64[sys];
     dfcplx* D = xdf[sys];
     for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
         const double2 x = X[i];
-        const double xr = x.x * down, xi = x.y * down;
-        const float hr = __double2float_rn(xr), hi = __double2float_rn(xi);
         dfcplx v;
-        v.x = dfloat(hr, __double2float_rn(xr - (double)hr));
-        v.y = dfloat(hi, __double2float_rn(xi - (double)hi));
+        v.x = df_split(x.x, e);
+        v.y = df_split(x.y, e);
         D[i] = v;
     }
 }

@@ -46,6 +46,7 @@ struct MixState {
     unsigned int counter;
     double xnorm2;      // ||x||^2 of the initial iterate
     int pexp;           // double-float residual apply: x entered scaled by 2^-pexp
+    int rpair;          // the residual buffer holds double-float pairs scaled by 2^-pexp
 };
 
 struct Partials {
@@ -79,7 +80,8 @@ cudaError_t mix_residual(const double2* const* b, const double2* const* ax, doub
                          bool pair = false);
 // x (complex128) -> double-float pairs scaled by the power of two 2^-pexp that brings the RMS of b
 // (of x before b is known) near 1, recorded in ms.pexp; systems with ms.run == 0 are skipped.
-// pair residuals (mix_residual with pair) read A x as double-float pairs and scale back by 2^pexp.
+// With pair, mix_residual reads A x as double-float pairs at that scale and leaves r = b - A x as
+// pairs at the same scale (ms.rpair), which mix_down normalises to complex64.
 cudaError_t mix_to_pair(const double2* const* x64, dfcplx* const* xdf, MixState* ms, long long n, int nsys, int nblk,
                         cudaStream_t s, long long* nl);
 cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms, long long n, int nsys, int nblk,
