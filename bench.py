@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
     ap.add_argument("--kernel", default="diff", choices=["diff", "h"],
                     help="operator form: difference form (default) or sampled analytic H (Eq. 21 literally)")
+    ap.add_argument("--residual", default="df", choices=["df", "fp64"],
+                    help="mixed: arithmetic of the outer residual's apply (double-float pairs or FP64)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default FFT schedule (no autotuning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -321,6 +323,7 @@ def _config(args, wl, med):
     return {"workload": wl.name if not args.grid else f"{wl.name}@{args.grid}", "grid": list(med.n), "dx_m": med.h,
             "frequencies_hz": f"{f[0]:g}-{f[-1]:g} ({len(f)})", "systems_per_step": args.systems,
             "precision": args.precision, "kernel": args.kernel, "tol": wl.tol, "parallelism": "replicas",
+            "residual": (args.residual if args.kernel == "diff" else "fp64") if args.precision == "mixed" else None,
             "l2": "inputs larger than L2 (contrast, Green spectra and Krylov vectors exceed 126 MB)"}
 
 
@@ -350,7 +353,8 @@ def main():
     dC = torch.from_numpy(med.dC).cuda().contiguous()
     drho = torch.from_numpy(med.drho).cuda().contiguous()
     opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000,
-                                kernel=lsm.LSM_KERNEL_H if args.kernel == "h" else lsm.LSM_KERNEL_DIFF)
+                                kernel=lsm.LSM_KERNEL_H if args.kernel == "h" else lsm.LSM_KERNEL_DIFF,
+                                residual=lsm.LSM_RESIDUAL_FP64 if args.residual == "fp64" else lsm.LSM_RESIDUAL_DFLOAT)
     if args.inner_tol:
         opts.inner_tol = args.inner_tol
     handles = {}
@@ -431,7 +435,7 @@ def main():
     # With the double-float residual (mixed, difference form) the FP64 slots time the pair apply:
     # its model flops are those of the FP64 form, each carried out as several FP32 operations, so
     # it is given against the HBM floor of its bytes and its FP64-equivalent rate, with no ALU frac.
-    pair = prec == lsm.LSM_MIXED and args.kernel == "diff"
+    pair = prec == lsm.LSM_MIXED and args.kernel == "diff" and args.residual == "df"
     peak, peak_kind = peaks()
     stages = []
     for slot in range(12):
