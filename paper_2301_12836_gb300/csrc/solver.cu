@@ -19,6 +19,30 @@ int vec_blocks(long long n) {
     return (int)b;
 }
 
+// Grid-stride loop over [0, n) in the order i0, i0 + S, i0 + 2 S, ... (S = threads of the grid's
+// x dimension), four indices at a time: ld(i) reads element i's operands, use(i, v) consumes them
+// in index order.  The four reads issue before the first use, so every thread keeps four
+// independent loads in flight (one at a time left these streams latency-bound); each thread still
+// visits its elements in the same order, so every sum is bitwise the same.
+template <class Ld, class Use>
+__device__ __forceinline__ void strided4(long long n, Ld ld, Use use) {
+    const long long S = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * S < n; i += 4 * S) {
+        const auto v0 = ld(i);
+        const auto v1 = ld(i + S);
+        const auto v2 = ld(i + 2 * S);
+        const auto v3 = ld(i + 3 * S);
+        use(i, v0);
+        use(i + S, v1);
+        use(i + 2 * S, v2);
+        use(i + 3 * S, v3);
+    }
+    for (; i < n; i += S) use(i, ld(i));
+}
+template <typename C> struct Two { C a, b; };
+template <typename C> struct Three { C a, b, c; };
+
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -174,16 +198,15 @@ __global__ void __launch_bounds__(VTH) k_bcg_init(const BcgVecs<T>* __restrict__
     if (skip && skip[sys].done) return;
     const BcgVecs<T> V = vecs[sys];
     Sums<C, 2> acc;
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const C b = V.b[i];
-        C r = b;
-        if (!x_zero) r = csub(b, V.v[i]);
-        V.r[i] = r;
-        V.rh[i] = r;
-        acc_nrm(acc, 0, b);
-        acc_nrm(acc, 1, r);
-        acc.step();
-    }
+    strided4(n, [&](long long i) { return Two<C>{V.b[i], x_zero ? czero<C>() : V.v[i]}; },
+             [&](long long i, const Two<C>& w) {
+                 const C r = x_zero ? w.a : csub(w.a, w.b);
+                 V.r[i] = r;
+                 V.rh[i] = r;
+                 acc_nrm(acc, 0, w.a);
+                 acc_nrm(acc, 1, r);
+                 acc.step();
+             });
     double v[2], tot[2];
     acc.finish(v);
     if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
@@ -209,14 +232,15 @@ __global__ void __launch_bounds__(VTH) k_bcg_p(const BcgVecs<T>* __restrict__ ve
     if (!S.active) return;
     const BcgVecs<T> V = vecs[sys];
     if (S.iters == 0) {
-        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) V.p[i] = V.r[i];
+        strided4(n, [&](long long i) { return V.r[i]; }, [&](long long i, const C& r) { V.p[i] = r; });
         return;
     }
     const C be = from_d2<C>(S.beta), om = from_d2<C>(S.omega);
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const C pv = csub(V.p[i], cmul(om, V.v[i]));
-        V.p[i] = cadd(V.r[i], cmul(be, pv));
-    }
+    strided4(n, [&](long long i) { return Three<C>{V.p[i], V.v[i], V.r[i]}; },
+             [&](long long i, const Three<C>& w) {
+                 const C pv = csub(w.a, cmul(om, w.b));
+                 V.p[i] = cadd(w.c, cmul(be, pv));
+             });
 }
 
 template <typename T>
@@ -227,10 +251,11 @@ __global__ void __launch_bounds__(VTH) k_bcg_alpha(const BcgVecs<T>* __restrict_
     if (!st[sys].run_v) return;
     const BcgVecs<T> V = vecs[sys];
     Sums<C, 2> acc;
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        acc_dot(acc, 0, V.rh[i], V.v[i]);
-        acc.step();
-    }
+    strided4(n, [&](long long i) { return Two<C>{V.rh[i], V.v[i]}; },
+             [&](long long, const Two<C>& w) {
+                 acc_dot(acc, 0, w.a, w.b);
+                 acc.step();
+             });
     double v[2], tot[2];
     acc.finish(v);
     if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
@@ -256,12 +281,13 @@ __global__ void __launch_bounds__(VTH) k_bcg_s(const BcgVecs<T>* __restrict__ ve
     const BcgVecs<T> V = vecs[sys];
     const C al = from_d2<C>(st[sys].alpha);
     Sums<C, 1> acc;
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const C s = csub(V.r[i], cmul(al, V.v[i]));
-        V.s[i] = s;
-        acc_nrm(acc, 0, s);
-        acc.step();
-    }
+    strided4(n, [&](long long i) { return Two<C>{V.r[i], V.v[i]}; },
+             [&](long long i, const Two<C>& w) {
+                 const C s = csub(w.a, cmul(al, w.b));
+                 V.s[i] = s;
+                 acc_nrm(acc, 0, s);
+                 acc.step();
+             });
     double v[1], tot[1];
     acc.finish(v);
     if (grid_sum<1>(v, pt, sys, &st[sys].counter, tot)) {
@@ -282,12 +308,12 @@ __global__ void __launch_bounds__(VTH) k_bcg_omega(const BcgVecs<T>* __restrict_
     if (!st[sys].run_t) return;
     const BcgVecs<T> V = vecs[sys];
     Sums<C, 3> acc;
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const C t = V.t[i];
-        acc_dot(acc, 0, t, V.s[i]);
-        acc_nrm(acc, 2, t);
-        acc.step();
-    }
+    strided4(n, [&](long long i) { return Two<C>{V.t[i], V.s[i]}; },
+             [&](long long, const Two<C>& w) {
+                 acc_dot(acc, 0, w.a, w.b);
+                 acc_nrm(acc, 2, w.a);
+                 acc.step();
+             });
     double v[3], tot[3];
     acc.finish(v);
     if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) {
@@ -311,18 +337,19 @@ __global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ v
     const C om = from_d2<C>(st[sys].omega);
     Sums<C, 3> acc;
     if (half) {
-        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH)
-            V.x[i] = cadd(V.x[i], cmul(al, V.p[i]));
+        strided4(n, [&](long long i) { return Two<C>{V.x[i], V.p[i]}; },
+                 [&](long long i, const Two<C>& w) { V.x[i] = cadd(w.a, cmul(al, w.b)); });
     } else {
-        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-            const C s = V.s[i], t = V.t[i];
-            V.x[i] = cadd(V.x[i], cadd(cmul(al, V.p[i]), cmul(om, s)));
-            const C r = csub(s, cmul(om, t));
-            V.r[i] = r;
-            acc_nrm(acc, 0, r);
-            acc_dot(acc, 1, V.rh[i], r);
-            acc.step();
-        }
+        struct Five { C s, t, x, p, rh; };
+        strided4(n, [&](long long i) { return Five{V.s[i], V.t[i], V.x[i], V.p[i], V.rh[i]}; },
+                 [&](long long i, const Five& w) {
+                     V.x[i] = cadd(w.x, cadd(cmul(al, w.p), cmul(om, w.s)));
+                     const C r = csub(w.s, cmul(om, w.t));
+                     V.r[i] = r;
+                     acc_nrm(acc, 0, r);
+                     acc_dot(acc, 1, w.rh, r);
+                     acc.step();
+                 });
     }
     double v[3], tot[3];
     acc.finish(v);
@@ -380,26 +407,25 @@ __global__ void __launch_bounds__(VTH) k_mix_res(const double2* const* __restric
     double v[2] = {0.0, 0.0};
     if (pair) {
         float sb = 0.f, sr = 0.f;
-        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-            const double2 bb = B[i];
-            const float4 p = reinterpret_cast<const float4*>(AX)[i];
-            const dfloat br = df_split(bb.x, pexp), bi = df_split(bb.y, pexp);
-            const dfloat rr = br - dfloat(p.x, p.y), ri = bi - dfloat(p.z, p.w);
-            reinterpret_cast<float4*>(R)[i] = make_float4(rr.hi, rr.lo, ri.hi, ri.lo);
-            sb = __fmaf_rn(br.hi, br.hi, __fmaf_rn(bi.hi, bi.hi, sb));
-            sr = __fmaf_rn(rr.hi, rr.hi, __fmaf_rn(ri.hi, ri.hi, sr));
-        }
+        struct BA { double2 b; float4 a; };
+        strided4(n, [&](long long i) { return BA{B[i], reinterpret_cast<const float4*>(AX)[i]}; },
+                 [&](long long i, const BA& w) {
+                     const dfloat br = df_split(w.b.x, pexp), bi = df_split(w.b.y, pexp);
+                     const dfloat rr = br - dfloat(w.a.x, w.a.y), ri = bi - dfloat(w.a.z, w.a.w);
+                     reinterpret_cast<float4*>(R)[i] = make_float4(rr.hi, rr.lo, ri.hi, ri.lo);
+                     sb = __fmaf_rn(br.hi, br.hi, __fmaf_rn(bi.hi, bi.hi, sb));
+                     sr = __fmaf_rn(rr.hi, rr.hi, __fmaf_rn(ri.hi, ri.hi, sr));
+                 });
         v[0] = (double)sb;
         v[1] = (double)sr;
     } else {
-        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-            const double2 bb = B[i];
-            const double2 a = xz ? make_double2(0.0, 0.0) : AX[i];
-            const double2 r = make_double2(bb.x - a.x, bb.y - a.y);
-            R[i] = r;
-            v[0] += bb.x * bb.x + bb.y * bb.y;
-            v[1] += r.x * r.x + r.y * r.y;
-        }
+        strided4(n, [&](long long i) { return Two<double2>{B[i], xz ? make_double2(0.0, 0.0) : AX[i]}; },
+                 [&](long long i, const Two<double2>& w) {
+                     const double2 r = make_double2(w.a.x - w.b.x, w.a.y - w.b.y);
+                     R[i] = r;
+                     v[0] += w.a.x * w.a.x + w.a.y * w.a.y;
+                     v[1] += r.x * r.x + r.y * r.y;
+                 });
     }
     double tot[2];
     if (grid_sum<2>(v, pt, sys, &ms[sys].counter, tot)) {
@@ -420,10 +446,8 @@ __global__ void __launch_bounds__(VTH) k_mix_xnorm(const double2* const* __restr
     const int sys = blockIdx.y;
     const double2* X = x64[sys];
     double v[1] = {0.0};
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const double2 x = X[i];
-        v[0] += x.x * x.x + x.y * x.y;
-    }
+    strided4(n, [&](long long i) { return X[i]; },
+             [&](long long, const double2& x) { v[0] += x.x * x.x + x.y * x.y; });
     double tot[1];
     if (grid_sum<1>(v, pt, sys, &ms[sys].counter, tot)) {
         ms[sys].xnorm2 = tot[0];
@@ -443,16 +467,12 @@ __global__ void __launch_bounds__(VTH) k_mix_down(double2* const* __restrict__ r
         // pairs at scale 2^-pexp: the high word times 2^pexp / ||r|| in FP32 (the low word is
         // below the FP32 rounding of the result)
         const float s32 = (float)(ldexp(1.0, ms[sys].pexp) * sc);
-        for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-            const float4 p = reinterpret_cast<const float4*>(R)[i];
-            D[i] = make_float2(__fmul_rn(p.x, s32), __fmul_rn(p.z, s32));
-        }
+        strided4(n, [&](long long i) { return reinterpret_cast<const float4*>(R)[i]; },
+                 [&](long long i, const float4& p) { D[i] = make_float2(__fmul_rn(p.x, s32), __fmul_rn(p.z, s32)); });
         return;
     }
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const double2 r = R[i];
-        D[i] = make_float2((float)(r.x * sc), (float)(r.y * sc));
-    }
+    strided4(n, [&](long long i) { return R[i]; },
+             [&](long long i, const double2& r) { D[i] = make_float2((float)(r.x * sc), (float)(r.y * sc)); });
 }
 
 __global__ void __launch_bounds__(VTH) k_mix_to_pair(const double2* const* __restrict__ x64, dfcplx* const* __restrict__ xdf,
@@ -467,13 +487,13 @@ __global__ void __launch_bounds__(VTH) k_mix_to_pair(const double2* const* __res
     if (blockIdx.x == 0 && threadIdx.x == 0) ms[sys].pexp = e;
     const double2* X = x64[sys];
     dfcplx* D = xdf[sys];
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const double2 x = X[i];
-        dfcplx v;
-        v.x = df_split(x.x, e);
-        v.y = df_split(x.y, e);
-        D[i] = v;
-    }
+    strided4(n, [&](long long i) { return X[i]; },
+             [&](long long i, const double2& x) {
+                 dfcplx v;
+                 v.x = df_split(x.x, e);
+                 v.y = df_split(x.y, e);
+                 D[i] = v;
+             });
 }
 
 __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64, float2* const* __restrict__ d32,
@@ -484,13 +504,14 @@ __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64
     double2* X = x64[sys];
     const float2* D = d32[sys];
     if (blockIdx.x == 0 && threadIdx.x == 0) ms[sys].xzero = 0;
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        const float2 d = D[i];
-        double2 x = X[i];
-        x.x += sc * (double)d.x;
-        x.y += sc * (double)d.y;
-        X[i] = x;
-    }
+    struct XD { double2 x; float2 d; };
+    strided4(n, [&](long long i) { return XD{X[i], D[i]}; },
+             [&](long long i, const XD& w) {
+                 double2 x = w.x;
+                 x.x += sc * (double)w.d.x;
+                 x.y += sc * (double)w.d.y;
+                 X[i] = x;
+             });
 }
 
 // conj(a) . b of complex64 vectors with the inner-product accumulation of the FP32 solver kernels:
@@ -498,10 +519,11 @@ __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64
 __global__ void __launch_bounds__(VTH) k_dot_c64(const float2* __restrict__ a, const float2* __restrict__ b, long long n,
                                                  double* __restrict__ partial) {
     Sums<float2, 2> acc;
-    for (long long i = (long long)blockIdx.x * VTH + threadIdx.x; i < n; i += (long long)gridDim.x * VTH) {
-        acc_dot(acc, 0, a[i], b[i]);
-        acc.step();
-    }
+    strided4(n, [&](long long i) { return Two<float2>{a[i], b[i]}; },
+             [&](long long, const Two<float2>& w) {
+                 acc_dot(acc, 0, w.a, w.b);
+                 acc.step();
+             });
     double v[2];
     acc.finish(v);
     __shared__ double sh[32 * 2];
