@@ -485,8 +485,8 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
     constexpr int YS = A * TX + (((TX - A * TX) % E) + E) % E;       // row stride of Y[t][.]
     const int nin = in_off + in_count;    // rows of a padded line that can be nonzero (<= L)
     extern __shared__ unsigned char smem_raw[];
-    C* sY = reinterpret_cast<C*>(smem_raw);
-    C* sX = sY + A * YS;                  // [3][nin][TX] inputs of the system in flight
+    C* sY = reinterpret_cast<C*>(smem_raw);   // two exchange buffers of A * YS, used alternately
+    C* sX = sY + 2 * A * YS;              // [3][nin][TX] inputs of the system in flight
     C* sG = sX + 3 * nin * TX;            // [6][nz+1][TX] spectrum slice: a warp's reads are contiguous
     C* sW = sG + 6 * (d.nz + 1) * TX;     // twiddles exp(-2 pi i k / L), k < L
     const int lx = threadIdx.x % TX;
@@ -568,13 +568,14 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
 #pragma unroll
                 for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], lds_fresh(&sW[q * k1]));
             }
-            __syncthreads();   // the previous reads of sY are done (and, at c = 2, every read of sX)
-            if (c == 2 && sn < nsys) prefetch(sn);
+            // buffer c & 1 was last read two components ago, before the previous barrier
+            C* Y = sY + (c & 1) * A * YS;
 #pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) sY[q * YS + k1 * TX + lx] = v[k1];
+            for (int k1 = 0; k1 < A; ++k1) Y[q * YS + k1 * TX + lx] = v[k1];
             __syncthreads();
+            if (c == 2 && sn < nsys) prefetch(sn);   // every read of sX is done
 #pragma unroll
-            for (int t = 0; t < A; ++t) R[c][t] = sY[t * YS + q * TX + lx];
+            for (int t = 0; t < A; ++t) R[c][t] = Y[t * YS + q * TX + lx];
             dft_reg<A, -1>(R[c]);   // R[c][k2] = X_c[q + A k2]
         }
         if (fresh) {
@@ -610,13 +611,15 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
 #pragma unroll
                 for (int k1 = 1; k1 < A; ++k1) R[c][k1] = cmulc(R[c][k1], lds_fresh(&sW[q * k1]));
             }
-            __syncthreads();
+            // buffers continue the alternation: inverse c uses (c + 1) & 1, last read before the
+            // barrier of the component before
+            C* Y = sY + ((c + 1) & 1) * A * YS;
 #pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) sY[q * YS + k1 * TX + lx] = R[c][k1];
+            for (int k1 = 0; k1 < A; ++k1) Y[q * YS + k1 * TX + lx] = R[c][k1];
             __syncthreads();
             C v[A];
 #pragma unroll
-            for (int t = 0; t < A; ++t) v[t] = sY[t * YS + q * TX + lx];
+            for (int t = 0; t < A; ++t) v[t] = Y[t * YS + q * TX + lx];
             dft_reg_p<A, 1, A, A / 2 + 1>(v);   // outputs k < (A/2 + 1) A only (checked at launch)
             C* dc = dst + (long long)c * out_count * plane;
 #pragma unroll
@@ -1321,7 +1324,7 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
             constexpr int A = F::A_, TXR = 4;
             constexpr int E = 16;
             constexpr int YS = A * TXR + (((TXR - A * TXR) % E) + E) % E;
-            const size_t smr = ((size_t)A * YS + (size_t)3 * (in_off + in_count) * TXR + (size_t)6 * (d.nz + 1) * TXR +
+            const size_t smr = ((size_t)2 * A * YS + (size_t)3 * (in_off + in_count) * TXR + (size_t)6 * (d.nz + 1) * TXR +
                                 (size_t)A * A) * sizeof(C);
             smem_attr((const void*)k4z_reg<CONJ, A, TXR>, smr);
             k4z_reg<CONJ, A, TXR><<<dim3(cdiv(d.Lx, TXR), d.Ly, 1), TXR * A, smr, st>>>(
