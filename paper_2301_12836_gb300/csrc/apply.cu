@@ -830,6 +830,109 @@ __global__ void __launch_bounds__(NL * FourStep<A LSM_COMMA B>::TPL, sizeof(T) =
     }
 }
 
+// Two-step FFT of contiguous rows for L = A * A with each line held by A consecutive lanes of one
+// warp: lane q owns the step-1 DFT of t = q and the step-2 DFT of k1 = q.  Step 1 loads its inputs
+// x[t + A a] straight from global memory (for each a the line's lanes read A consecutive
+// elements), the transpose between the steps goes through a shared-memory tile private to the
+// line (row stride A + 1: conflict-free both ways) ordered by __syncwarp, and step 2 leaves
+// X[k1 + A k2] in registers for a coalesced store.  No block barrier and one shared-memory round
+// trip per element (the tile-transposing kernels above make three).  The arithmetic is that of
+// fft4_smem, operation for operation, so results are bitwise those of k4_rows / k4_fftx_out.
+template <int A, typename C>
+__device__ __forceinline__ void rows_w_exchange(C (&v)[A], C* tl, int q) {
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) tl[q * (A + 1) + k1] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < A; ++t) v[t] = tl[t * (A + 1) + q];
+}
+
+// forward x FFT of zero-padded rows: row r of src (in_count elements, the rest zero, at most
+// (A/2 + 1) A of them) -> row r of dst (L elements)
+template <typename T, int A, int LPB>
+__global__ void __launch_bounds__(LPB * A) k4_rows_w(const typename cplx_of<T>::type* __restrict__ tw,
+                                                     const ApplySys<T>* __restrict__ sys, int src_sel, int dst_sel,
+                                                     long long nrows, int in_count) {
+    typedef typename cplx_of<T>::type C;
+    constexpr int L = A * A;
+    __shared__ C tile[LPB][A * (A + 1)];
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    const int ln = threadIdx.x / A, q = threadIdx.x % A;
+    const long long row = (long long)blockIdx.x * LPB + ln;
+    const bool live = row < nrows;
+    const C* __restrict__ src = pick<C>(S, src_sel) + row * in_count;
+    C* __restrict__ dst = pick<C>(S, dst_sel) + row * L;
+    C v[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+        const int e = q + A * a;
+        v[a] = (a < A / 2 + 1 && live && e < in_count) ? src[e] : czero<C>();
+    }
+    dft_reg_p<A, -1, A / 2 + 1, A>(v);
+    if (q) {
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[q * k1]));
+    }
+    rows_w_exchange<A>(v, tile[ln], q);
+    dft_reg_p<A, -1, A, A>(v);
+    if (live) {
+#pragma unroll
+        for (int k2 = 0; k2 < A; ++k2) dst[q + A * k2] = v[k2];
+    }
+}
+
+// inverse x FFT of the rows of w2 [3][nz][ny][L], crop to x = k - xoff in [0, nx) (at most
+// (A/2 + 1) A outputs), Au = u - u_s
+template <typename T, int A, int LPB>
+__global__ void __launch_bounds__(LPB * A) k4_xout_w(Dims d, const ApplySys<T>* __restrict__ sys,
+                                                     const typename cplx_of<T>::type* __restrict__ tw, int xoff) {
+    typedef typename cplx_of<T>::type C;
+    constexpr int L = A * A, NO = A / 2 + 1;
+    __shared__ C tile[LPB][A * (A + 1)];
+    const ApplySys<T> S = sys[blockIdx.y];
+    if (S.run && !*S.run) return;
+    const int ln = threadIdx.x / A, q = threadIdx.x % A;
+    const long long nrows = 3LL * d.nz * d.ny;
+    const long long row = (long long)blockIdx.x * LPB + ln;
+    const bool live = row < nrows;
+    const C* __restrict__ src = S.w2 + row * L;
+    const C* __restrict__ uin = S.u + row * d.nx;
+    C* __restrict__ out = S.out + row * d.nx;
+    C v[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) v[a] = live ? src[q + A * a] : czero<C>();
+    // FP32: u for the epilogue is fetched now, so its latency overlaps the transform
+    constexpr bool PRE = sizeof(T) == 4;
+    C uo[PRE ? NO : 1];
+    if constexpr (PRE) {
+#pragma unroll
+        for (int k2 = 0; k2 < NO; ++k2) {
+            const int x = q + A * k2 - xoff;
+            uo[k2] = (live && x >= 0 && x < d.nx) ? uin[x] : czero<C>();
+        }
+    }
+    dft_reg_p<A, 1, A, A>(v);
+    if (q) {
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) {
+            C w = __ldg(&tw[q * k1]);
+            w.y = -w.y;
+            v[k1] = cmul(v[k1], w);
+        }
+    }
+    rows_w_exchange<A>(v, tile[ln], q);
+    dft_reg_p<A, 1, A, NO>(v);
+    if (live) {
+#pragma unroll
+        for (int k2 = 0; k2 < NO; ++k2) {
+            const int x = q + A * k2 - xoff;
+            if (x >= 0 && x < d.nx) out[x] = csub(PRE ? uo[PRE ? k2 : 0] : uin[x], v[k2]);
+        }
+    }
+    if (S.count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(S.count, 1ull);
+}
+
 // four-step inverse x FFT + crop + Au = u - u_s; ROWS rows x 3 components per block; src w2.
 template <typename T, int A, int B, int ROWS>
 __global__ void __launch_bounds__(3 * ROWS * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 8 ? 3 : 2) k4_fftx_out(Dims d, const ApplySys<T>* __restrict__ sys,
@@ -1211,7 +1314,11 @@ static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const P
     const long long nrows = 3LL * d.ez * d.ey;
     with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
         using F = decltype(eng);
-        if constexpr (F::INPLACE) {
+        if constexpr (F::INPLACE && F::A_ == F::B_) {
+            constexpr int A = F::A_, LPB = sizeof(T) == 4 ? 16 : 8;
+            k4_rows_w<T, A, LPB><<<dim3(cdiv(nrows, LPB), nsys), LPB * A, 0, st>>>((const C*)pl.twx, sys, 3, 2, nrows,
+                                                                                   d.ex);
+        } else if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 8 : 12;
             const size_t sm = (size_t)A * B * (NL + 1) * sizeof(C);
             smem_attr((const void*)k4_rows<T, -1, A, B, NL>, sm);
@@ -1235,7 +1342,11 @@ static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, con
     typedef typename cplx_of<T>::type C;
     with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
         using F = decltype(eng);
-        if constexpr (F::INPLACE) {
+        if constexpr (F::INPLACE && F::A_ == F::B_) {
+            constexpr int A = F::A_, LPB = sizeof(T) == 4 ? 16 : 8;
+            const long long nrows = 3LL * d.nz * d.ny;
+            k4_xout_w<T, A, LPB><<<dim3(cdiv(nrows, LPB), nsys), LPB * A, 0, st>>>(d, sys, (const C*)pl.twx, xoff);
+        } else if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, ROWS = sizeof(T) == 4 ? 8 : 4;
             const size_t sm = (size_t)A * B * (3 * ROWS + 1) * sizeof(C);
             smem_attr((const void*)k4_fftx_out<T, A, B, ROWS>, sm);
