@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(NTH) k_strided_raw(FftPlan p, const typename c
 // four-step strided pass: step 1 loads straight from global memory, the last step stores straight
 // to global memory; one shared-memory exchange in between.  Block = TX * TPL threads, line l = lx.
 template <typename T, int DIR, int A, int B, int TX>
-__global__ void __launch_bounds__(TX * FourStep<A LSM_COMMA B>::TPL, sizeof(T) == 8 ? 4 : 2) k4_strided(const typename cplx_of<T>::type* __restrict__ tw,
+__global__ void __launch_bounds__(TX * FourStep<A LSM_COMMA B>::TPL, 4) k4_strided(const typename cplx_of<T>::type* __restrict__ tw,
                                                                      StridedArgs a, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ unsigned char smem_raw[];
@@ -1553,7 +1553,11 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
         const long long nrows = 9LL * d.nz * d.ny;
         with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
             using F = decltype(eng);
-            if constexpr (F::INPLACE) {
+            if constexpr (F::INPLACE && F::A_ == F::B_) {
+                constexpr int A = F::A_, LPB = sizeof(T) == 4 ? 16 : 8;
+                k4_rows_w<T, A, LPB><<<dim3(cdiv(nrows, LPB), nsys), LPB * A, 0, st>>>((const C*)pl.twx, sys, 2, 3,
+                                                                                       nrows, d.nx);
+            } else if constexpr (F::INPLACE) {
                 constexpr int A = F::A_, B = F::B_, NL = sizeof(T) == 4 ? 8 : 12;
                 const size_t sm = (size_t)A * B * (NL + 1) * sizeof(C);
                 smem_attr((const void*)k4_rows<T, -1, A, B, NL>, sm);
