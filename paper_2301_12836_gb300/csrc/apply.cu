@@ -738,7 +738,7 @@ __global__ void LSM_FFT_BOUND(T, F) k_fftx_out(Dims d, const ApplySys<T>* __rest
 // (index p holds node p - 1).  sigma in w1, q written to w2.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NTH) k_divq(Dims d, const T* __restrict__ drho, const ApplySys<T>* __restrict__ sys) {
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_divq(Dims d, const T* __restrict__ drho, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
     const ApplySys<T> S = sys[blockIdx.y];
     if (S.run && !*S.run) return;
