@@ -326,10 +326,10 @@ lsm_status lsm_dot_c64(lsm_t h, long long n, const void *a, const void *b, doubl
  * contraction, 1 contrast source + x FFT, 2 y FFT, 3 z FFT + Green multiply + inverse z FFT,
  * 4 inverse y FFT, 5 inverse x FFT + epilogue.  Synchronises the stream.
  * lsm_timer_read: synchronise, then write total milliseconds and launches per slot
- * (slot = 6 * p + stage, p = 0 for FP64 applies, 1 for FP32 applies) and the number of
- * system-level operator applies executed in FP64 (applies[0]) and FP32 (applies[1]) since
- * lsm_timer_start; systems masked out of a batched launch are not counted.  Any out-pointer
- * may be NULL.
+ * (slot = 6 * p + stage, p = 0 for FP64 applies and the mixed solver's double-float residual
+ * applies, 1 for FP32 applies) and the number of system-level operator applies executed in
+ * FP64 or double-float (applies[0]) and FP32 (applies[1]) since lsm_timer_start; systems masked
+ * out of a batched launch are not counted.  Any out-pointer may be NULL.
  */
 lsm_status lsm_timer_start(lsm_t h, int enable);
 lsm_status lsm_timer_read(lsm_t h, double ms[12], long long launches[12], long long applies[2]);
