@@ -208,7 +208,9 @@ lsm_status lsm_adjoint(lsm_t h, const void *v, void *AHv);
  *   x       device complex128, 3 * nz*ny*nx; on entry the initial guess (zeros for
  *           none), on exit the solution (the last iterate on LSM_ERR_NOCONV)
  *   iters   host int* or NULL: BiCGSTAB iterations (mixed: total inner iterations)
- *   relres  host double* or NULL: true FP64 residual ||b - A x|| / ||b|| at exit
+ *   relres  host double* or NULL: the true residual ||b - A x|| / ||b|| at exit, from an
+ *           FP64 apply (LSM_FP64) or the mixed mode's residual apply (double-float by
+ *           default, see lsm_opts.residual), not the recursively updated one
  * Synchronises the handle's stream.
  */
 lsm_status lsm_solve(lsm_t h, const void *b, void *x, int *iters, double *relres);
