@@ -22,7 +22,31 @@ constexpr int MAXM = 8;   // moment tensors per source launch
 struct GreenPar {
     double a, b, rho, w;   // P, S velocities, density, angular frequency
     int mode;              // 0 exact, 1 paper
+    // derived on the host (make_green_par), so that no node divides by them again
+    double c4;             // 1 / (4 pi rho)
+    double ka, kb;         // w / a, w / b
+    double ia2, ib2;       // 1 / a^2, 1 / b^2
+    double ika2, ikb2;     // 1 / ka^2, 1 / kb^2
+    double cn;             // static term of the paper's near field (mode 1)
 };
+
+static GreenPar make_green_par(double lam, double mu, double rho, double omega, int green) {
+    GreenPar p;
+    p.a = sqrt((lam + 2.0 * mu) / rho);
+    p.b = sqrt(mu / rho);
+    p.rho = rho;
+    p.w = omega;
+    p.mode = green;
+    p.c4 = 1.0 / (4.0 * M_PI * rho);
+    p.ka = omega / p.a;
+    p.kb = omega / p.b;
+    p.ia2 = 1.0 / (p.a * p.a);
+    p.ib2 = 1.0 / (p.b * p.b);
+    p.ika2 = 1.0 / (p.ka * p.ka);
+    p.ikb2 = 1.0 / (p.kb * p.kb);
+    p.cn = (1.0 - p.b * p.b * p.ia2) / (8.0 * M_PI * rho) * p.ib2;
+    return p;
+}
 
 __device__ __forceinline__ double2 cexpi(double phase) {
     double s, c;
@@ -30,8 +54,9 @@ __device__ __forceinline__ double2 cexpi(double phase) {
     return make_double2(c, s);
 }
 
-// psi(x) = ((1 - i x) e^{ix} - 1) / x^2 = sum_m i^m (m+1)/(m+2)! x^m
-__device__ __forceinline__ double2 psi(double x) {
+// psi(x) = ((1 - i x) e^{ix} - 1) / x^2 = sum_m i^m (m+1)/(m+2)! x^m; e = e^{ix} and ix2 = 1/x^2
+// are supplied by the caller (it has them already)
+__device__ __forceinline__ double2 psi(double x, double2 e, double ix2) {
     if (fabs(x) < 0.5) {
         // coefficients (m+1)/(m+2)! for m = 0..14
         const double a[15] = {1.0 / 2.0, 2.0 / 6.0, 3.0 / 24.0, 4.0 / 120.0, 5.0 / 720.0, 6.0 / 5040.0,
@@ -45,25 +70,21 @@ __device__ __forceinline__ double2 psi(double x) {
         for (int m = 13; m >= 1; m -= 2) im = im * (-x2) + a[m];
         return make_double2(re, im * x);
     }
-    const double2 e = cexpi(x);
-    const double x2 = x * x;
-    return make_double2((e.x + x * e.y - 1.0) / x2, (e.y - x * e.x) / x2);
+    return make_double2((e.x + x * e.y - 1.0) * ix2, (e.y - x * e.x) * ix2);
 }
 
-// f, g and their radial derivatives at distance r
-__device__ void radial(const GreenPar& p, double r, double2& f, double2& g, double2& fp, double2& gp) {
-    const double c4 = 1.0 / (4.0 * M_PI * p.rho);
-    const double ka = p.w / p.a, kb = p.w / p.b;
-    const double ia2 = 1.0 / (p.a * p.a), ib2 = 1.0 / (p.b * p.b);
+// f, g and their radial derivatives at distance r (ir = 1 / r)
+__device__ void radial(const GreenPar& p, double r, double ir, double2& f, double2& g, double2& fp, double2& gp) {
+    const double c4 = p.c4, ka = p.ka, kb = p.kb, ia2 = p.ia2, ib2 = p.ib2;
     const double2 ea = cexpi(ka * r), eb = cexpi(kb * r);
-    const double ir = 1.0 / r;
     // E_c = e_c / r and E_c' = (i k_c - 1/r) E_c
     const double2 Ea = make_double2(ea.x * ir, ea.y * ir);
     const double2 Eb = make_double2(eb.x * ir, eb.y * ir);
     const double2 Eap = make_double2(-ka * Ea.y - ir * Ea.x, ka * Ea.x - ir * Ea.y);
     const double2 Ebp = make_double2(-kb * Eb.y - ir * Eb.x, kb * Eb.x - ir * Eb.y);
     if (p.mode == 0) {
-        const double2 pa = psi(ka * r), pb = psi(kb * r);
+        const double ir2 = ir * ir;
+        const double2 pa = psi(ka * r, ea, p.ika2 * ir2), pb = psi(kb * r, eb, p.ikb2 * ir2);
         const double2 Q = make_double2((pb.x * ib2 - pa.x * ia2) * ir, (pb.y * ib2 - pa.y * ia2) * ir);
         const double2 Qp = make_double2((eb.x * ib2 - ea.x * ia2) * ir * ir - 3.0 * Q.x * ir,
                                         (eb.y * ib2 - ea.y * ia2) * ir * ir - 3.0 * Q.y * ir);
@@ -72,7 +93,7 @@ __device__ void radial(const GreenPar& p, double r, double2& f, double2& g, doub
         fp = make_double2(c4 * (Ebp.x * ib2 - Qp.x), c4 * (Ebp.y * ib2 - Qp.y));
         gp = make_double2(c4 * (Eap.x * ia2 - Ebp.x * ib2 + 3.0 * Qp.x), c4 * (Eap.y * ia2 - Ebp.y * ib2 + 3.0 * Qp.y));
     } else {
-        const double cn = (1.0 - p.b * p.b * ia2) / (8.0 * M_PI * p.rho) * ib2;
+        const double cn = p.cn;
         f = make_double2(c4 * Eb.x * ib2 - cn * ir, c4 * Eb.y * ib2);
         g = make_double2(c4 * (Ea.x * ia2 - Eb.x * ib2) + 3.0 * cn * ir, c4 * (Ea.y * ia2 - Eb.y * ib2));
         fp = make_double2(c4 * Ebp.x * ib2 + cn * ir * ir, c4 * Ebp.y * ib2);
@@ -100,9 +121,10 @@ __global__ void k_green_table(Dims d, GreenPar p, double2 self, double2* __restr
             } else {
                 const double x[3] = {mx * d.h, my * d.h, mz * d.h};
                 const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-                const double gx = x[0] / r, gy = x[1] / r, gz = x[2] / r;
+                const double ir = 1.0 / r;
+                const double gx = x[0] * ir, gy = x[1] * ir, gz = x[2] * ir;
                 double2 f, g, fp, gp;
-                radial(p, r, f, g, fp, gp);
+                radial(p, r, ir, f, g, fp, gp);
                 const double gg[6] = {gx * gx, gy * gy, gz * gz, gy * gz, gx * gz, gx * gy};
                 for (int c = 0; c < 6; ++c) {
                     const double dd = c < 3 ? 1.0 : 0.0;
@@ -134,10 +156,10 @@ __global__ void k_h_table(Dims d, GreenPar p, int i, double2* __restrict__ T) {
         if (ix != d.nx && iy != d.ny && iz != d.nz && (mx != 0 || my != 0 || mz != 0)) {
             const double x[3] = {mx * d.h, my * d.h, mz * d.h};
             const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-            const double c[3] = {x[0] / r, x[1] / r, x[2] / r};
-            double2 f, g, fp, gp;
-            radial(p, r, f, g, fp, gp);
             const double ir = 1.0 / r;
+            const double c[3] = {x[0] * ir, x[1] * ir, x[2] * ir};
+            double2 f, g, fp, gp;
+            radial(p, r, ir, f, g, fp, gp);
             // dG_ij/dx_k = f' c_k d_ij + g' c_i c_j c_k + (g / r)(d_ik c_j + d_jk c_i - 2 c_i c_j c_k)
             auto dG = [&](int a, int b, int k) -> double2 {
                 const double dab = a == b ? 1.0 : 0.0, dak = a == k ? 1.0 : 0.0, dbk = b == k ? 1.0 : 0.0;
@@ -183,10 +205,10 @@ __global__ void k_source(Dims d, GreenPar p, MomentSet ms, double sx, double sy,
             atomicExch(flag, 1);
             continue;
         }
-        const double g[3] = {x / r, y / r, z / r};
-        double2 f, gg, fp, gp;
-        radial(p, r, f, gg, fp, gp);
         const double ir = 1.0 / r;
+        const double g[3] = {x * ir, y * ir, z * ir};
+        double2 f, gg, fp, gp;
+        radial(p, r, ir, f, gg, fp, gp);
         const double2 A = make_double2(fp.x + gg.x * ir, fp.y + gg.y * ir);
         const double2 B = make_double2(gp.x - 2.0 * gg.x * ir, gp.y - 2.0 * gg.y * ir);
         const double2 Cc = make_double2(gg.x * ir, gg.y * ir);
@@ -222,10 +244,10 @@ __global__ void __launch_bounds__(256) k_source_grad(Dims d, GreenPar p, double 
         const double x = ix * d.h - sx, y = iy * d.h - sy, z = iz * d.h - sz;
         const double r = sqrt(x * x + y * y + z * z);
         if (r == 0.0) continue;  // u0 is zero on a node that coincides with the source
-        const double g[3] = {x / r, y / r, z / r};
-        double2 f, gg, fp, gp;
-        radial(p, r, f, gg, fp, gp);
         const double ir = 1.0 / r;
+        const double g[3] = {x * ir, y * ir, z * ir};
+        double2 f, gg, fp, gp;
+        radial(p, r, ir, f, gg, fp, gp);
         const double2 A = make_double2(fp.x + gg.x * ir, fp.y + gg.y * ir);
         const double2 B = make_double2(gp.x - 2.0 * gg.x * ir, gp.y - 2.0 * gg.y * ir);
         const double2 Cc = make_double2(gg.x * ir, gg.y * ir);
@@ -279,12 +301,7 @@ cudaError_t launch_extract_octant(const Dims& d, const double2* full, double2* o
 
 cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, double mu, double rho, double omega,
                                int green, int kernel, double2* scratch, double2* ghat64, cudaStream_t st, long long* nl) {
-    GreenPar p;
-    p.a = sqrt((lam + 2.0 * mu) / rho);
-    p.b = sqrt(mu / rho);
-    p.rho = rho;
-    p.w = omega;
-    p.mode = green;
+    const GreenPar p = make_green_par(lam, mu, rho, omega, green);
     // cell average of G over [-h/2, h/2]^3 times h^3, to O(w h): the static Kelvin part gives
     // (1/(3a^2) + 2/(3b^2)) C h^2 / (4 pi rho) with C = int_{unit cube} dV/|x| = 3 ln(2+sqrt3) - pi/2,
     // the r^0 term of the expansion gives i w h^3 (1/(3a^3) + 2/(3b^3)) / (4 pi rho).
@@ -318,12 +335,7 @@ cudaError_t launch_green_setup(const Dims& d, const Plans& pl64, double lam, dou
 
 cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, double omega, int green, int nm,
                           const double* M6, const double* xs, double2* const* u0, int* flag, cudaStream_t st, long long* nl) {
-    GreenPar p;
-    p.a = sqrt((lam + 2.0 * mu) / rho);
-    p.b = sqrt(mu / rho);
-    p.rho = rho;
-    p.w = omega;
-    p.mode = green;
+    const GreenPar p = make_green_par(lam, mu, rho, omega, green);
     for (int m0 = 0; m0 < nm; m0 += MAXM) {
         MomentSet ms;
         ms.nm = nm - m0 < MAXM ? nm - m0 : MAXM;
@@ -342,12 +354,7 @@ cudaError_t launch_source(const Dims& d, double lam, double mu, double rho, doub
 cudaError_t launch_source_gradient(const Dims& d, double lam, double mu, double rho, double omega, int green,
                                    const double* xs, const double2* lamv, double* partial, double* out, cudaStream_t st,
                                    long long* nl) {
-    GreenPar p;
-    p.a = sqrt((lam + 2.0 * mu) / rho);
-    p.b = sqrt(mu / rho);
-    p.rho = rho;
-    p.w = omega;
-    p.mode = green;
+    const GreenPar p = make_green_par(lam, mu, rho, omega, green);
     long long nb = (d.N + 255) / 256;
     if (nb > SG_BLOCKS) nb = SG_BLOCKS;
     if (nb < 1) nb = 1;
