@@ -147,7 +147,7 @@ __device__ __forceinline__ void stress_at(const Dims& d, const T* __restrict__ d
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTH) k_stress(Dims d, const T* __restrict__ dC, const ApplySys<T>* __restrict__ sys) {
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 8 : 1) k_stress(Dims d, const T* __restrict__ dC, const ApplySys<T>* __restrict__ sys) {
     typedef typename cplx_of<T>::type C;
     const ApplySys<T> S = sys[blockIdx.y];
     if (S.run && !*S.run) return;
