@@ -850,7 +850,7 @@ __device__ __forceinline__ void rows_w_exchange(C (&v)[A], C* tl, int q) {
 // forward x FFT of zero-padded rows: row r of src (in_count elements, the rest zero, at most
 // (A/2 + 1) A of them) -> row r of dst (L elements)
 template <typename T, int A, int LPB>
-__global__ void __launch_bounds__(LPB * A) k4_rows_w(const typename cplx_of<T>::type* __restrict__ tw,
+__global__ void __launch_bounds__(LPB * A, sizeof(T) == 4 ? 4 : 1) k4_rows_w(const typename cplx_of<T>::type* __restrict__ tw,
                                                      const ApplySys<T>* __restrict__ sys, int src_sel, int dst_sel,
                                                      long long nrows, int in_count) {
     typedef typename cplx_of<T>::type C;
