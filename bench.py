@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-fp64-residual", action="store_true",
+                    help="skip the side measurement of the mixed solve with the FP64 residual apply")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparator (context only)")
     return ap.parse_args()
 
@@ -529,6 +531,54 @@ def main():
         line["e2e"] = {"value": round((e64 + e32) / te, 3), "unit": "matvec/s",
                        "h2d_bytes_per_step": nsys * 9 * 8, "d2h_bytes_per_step": nsys * N3 * 16,
                        "solves_per_s": round(solves / te, 4)}
+
+    # the same K steps with the mixed solve's residual apply in FP64 (LSM_RESIDUAL_FP64), timed the
+    # same way (CUDA events, one untimed step first), beside the double-float headline
+    if pair and not args.no_fp64_residual and rank == 0:
+        dC = torch.from_numpy(med.dC).cuda().contiguous()
+        drho = torch.from_numpy(med.drho).cuda().contiguous()
+        o_r = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000, kernel=lsm.LSM_KERNEL_DIFF,
+                                   residual=lsm.LSM_RESIDUAL_FP64)
+        hr = {fidx[args.warmup]: lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho,
+                                                2 * np.pi * freqs[fidx[args.warmup]], o_r)}
+        del dC, drho
+        rbase = hr[fidx[args.warmup]]
+        for s in range(args.warmup, steps_total):
+            if fidx[s] not in hr:
+                hr[fidx[s]] = lsm.lsm_create_shared(rbase, 2 * np.pi * freqs[fidx[s]])
+        if schedule is not None:
+            lsm.lsm_set_schedule(rbase, lsm.LSM_FP64, schedule["fp64"])
+            lsm.lsm_set_schedule(rbase, lsm.LSM_MIXED, schedule["fp32"])
+        rr_max = []
+
+        def rstep(s):
+            h = hr[fidx[s]]
+            sources(h, b)
+            for j in range(nsys):
+                x[j].zero_()
+            code, its, rrs, sts = lsm.lsm_solve_batched([h] * nsys, b, x, check=False)
+            if code != lsm.LSM_OK:
+                raise RuntimeError(f"FP64-residual solve failed: {lsm.STATUS_NAMES.get(code)} {sts}")
+            rr_max.append(max(rrs))
+
+        rstep(args.warmup)
+        lsm.lsm_timer_start(rbase, False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(args.warmup, steps_total):
+            rstep(s)
+        e1.record()
+        torch.cuda.synchronize()
+        tr = e0.elapsed_time(e1) / 1e3
+        _, _, (r64, r32) = lsm.lsm_timer_read(rbase)
+        line["fp64_residual"] = {"value": round((r64 + r32) / tr, 3), "unit": "matvec/s",
+                                 "solves_per_s": round(solves / tr, 4), "ms_per_step": round(tr * 1e3 / args.steps, 3),
+                                 "dtype": "f32+f64", "relres_max": float(np.max(rr_max[1:])),
+                                 "note": "the mixed solve with its outer residual apply in FP64; same steps, "
+                                         "timed with CUDA events"}
+        del hr, rbase
 
     # the plain FP64 GPU form on the first frequency, for the precision comparison
     if prec == lsm.LSM_MIXED and not args.no_fp64_form and rank == 0:
