@@ -325,7 +325,7 @@ def _config(args, wl, med):
     return {"workload": wl.name if not args.grid else f"{wl.name}@{args.grid}", "grid": list(med.n), "dx_m": med.h,
             "frequencies_hz": f"{f[0]:g}-{f[-1]:g} ({len(f)})", "systems_per_step": args.systems,
             "precision": args.precision, "kernel": args.kernel, "tol": wl.tol, "parallelism": "replicas",
-            "residual": (args.residual if args.kernel == "diff" else "fp64") if args.precision == "mixed" else None,
+            "residual": args.residual if args.precision == "mixed" else None,
             "l2": "inputs larger than L2 (contrast, Green spectra and Krylov vectors exceed 126 MB)"}
 
 
@@ -434,10 +434,10 @@ def main():
     value = applies_all / (ms_max / 1e3)
     # per-stage rooflines: FP32 stages against HBM (algorithmic bytes), FP64 stages against the
     # FP64 pipe (model flops); the dominant stage (largest share of the timed region) is reported.
-    # With the double-float residual (mixed, difference form) the FP64 slots time the pair apply:
+    # With the double-float residual (mixed) the FP64 slots time the pair apply:
     # its model flops are those of the FP64 form, each carried out as several FP32 operations, so
     # it is given against the HBM floor of its bytes and its FP64-equivalent rate, with no ALU frac.
-    pair = prec == lsm.LSM_MIXED and args.kernel == "diff" and args.residual == "df"
+    pair = prec == lsm.LSM_MIXED and args.residual == "df"
     peak, peak_kind = peaks()
     stages = []
     for slot in range(12):
@@ -537,7 +537,7 @@ def main():
     if pair and not args.no_fp64_residual and rank == 0:
         dC = torch.from_numpy(med.dC).cuda().contiguous()
         drho = torch.from_numpy(med.drho).cuda().contiguous()
-        o_r = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000, kernel=lsm.LSM_KERNEL_DIFF,
+        o_r = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000, kernel=opts.kernel,
                                    residual=lsm.LSM_RESIDUAL_FP64)
         hr = {fidx[args.warmup]: lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho,
                                                 2 * np.pi * freqs[fidx[args.warmup]], o_r)}

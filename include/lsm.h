@@ -92,13 +92,12 @@ typedef struct {
                           density), 24 spectra (18 H, 6 G), about 4x the spectrum memory.  The
                           adjoint calls (lsm_adjoint, lsm_solve_adjoint, lsm_gradient) and
                           lsm_apply_static return LSM_ERR_ARG for it. */
-    int residual;      /* LSM_MIXED with LSM_KERNEL_DIFF: arithmetic of the outer residual's
-                          operator apply.  LSM_RESIDUAL_DFLOAT (default): double-float pairs
+    int residual;      /* LSM_MIXED: arithmetic of the outer residual's operator apply.  LSM_RESIDUAL_DFLOAT (default): double-float pairs
                           (two FP32 words, about 48 significand bits, unit roundoff near
                           2^-48; see lsm_apply_df) on the FP32 pipe, with the iterate scaled
                           by a power of two to RMS(b) ~ 1 first; LSM_RESIDUAL_FP64: FP64.
-                          Adjoint solves and LSM_KERNEL_H always use FP64.  Ignored for
-                          LSM_FP64 handles. */
+                          Adjoint solves always use FP64.  Ignored for LSM_FP64
+                          handles. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */
@@ -188,8 +187,8 @@ lsm_status lsm_apply_c64(lsm_t h, const void *u, void *Au);
  * (the mixed solver scales its iterate first; this entry point does not).
  *   u, Au  device complex128, 3 * nz*ny*nx; u != Au.  Au is written as
  *          complex128 (the pairs are converted in place at the end).
- * Only for handles created with LSM_MIXED, LSM_KERNEL_DIFF and
- * LSM_RESIDUAL_DFLOAT (else LSM_ERR_ARG).
+ * Either operator form (lsm_opts.kernel).  Only for handles created with
+ * LSM_MIXED and LSM_RESIDUAL_DFLOAT (else LSM_ERR_ARG).
  */
 lsm_status lsm_apply_df(lsm_t h, const void *u, void *Au);
 

@@ -1598,13 +1598,9 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
 template <typename T>
 cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sys, int nsys, cudaStream_t st,
                          long long* nl) {
-    // the double-float operator: difference form, default schedule
+    // the double-float operator runs the default schedule
     constexpr bool PAIR = std::is_same<T, dfloat>::value;
-    if constexpr (PAIR) {
-        if (m.kernel == 1) return cudaErrorInvalidValue;
-    } else {
-        if (m.kernel == 1) return launch_apply_h<T>(m, pl, sys, nsys, st, nl);
-    }
+    if (m.kernel == 1) return launch_apply_h<T>(m, pl, sys, nsys, st, nl);
     const Dims& d = m.d;
     const T* dC = (const T*)m.dC;
     const T* drho = (const T*)m.drho;

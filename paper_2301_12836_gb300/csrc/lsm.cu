@@ -296,7 +296,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     s->st = (cudaStream_t)stream;
     s->precision = o.precision;
     s->green = o.green;
-    s->pair = o.precision == LSM_MIXED && o.kernel == LSM_KERNEL_DIFF && o.residual == LSM_RESIDUAL_DFLOAT;
+    s->pair = o.precision == LSM_MIXED && o.residual == LSM_RESIDUAL_DFLOAT;
     s->lam = lambda0; s->mu = mu0; s->rho = rho0;
     Dims& d = s->d;
     d.nx = n[0]; d.ny = n[1]; d.nz = n[2];
@@ -484,7 +484,7 @@ extern "C" lsm_status lsm_apply_df(lsm_t h, const void* u, void* Au) {
     if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply_df: u and Au must be distinct non-null device buffers");
     Store* s = h->s;
     if (!s->pair)
-        return fail(h, LSM_ERR_ARG, "lsm_apply_df: needs a handle created with LSM_MIXED, LSM_KERNEL_DIFF, LSM_RESIDUAL_DFLOAT");
+        return fail(h, LSM_ERR_ARG, "lsm_apply_df: needs a handle created with LSM_MIXED and LSM_RESIDUAL_DFLOAT");
     lsm_status rc = ensure_apply_ws(h);
     if (rc != LSM_OK) return rc;
     const long long n3 = 3 * s->d.N;

@@ -49,12 +49,52 @@ def test_apply_df_green_paper_and_taper():
     assert rel(host(Au).reshape(u.shape), want) < 1e-11
 
 
+@pytest.mark.parametrize("n", [(16, 12, 10), (128, 6, 5)])
+@pytest.mark.parametrize("mode,green", [("exact", lsm.LSM_GREEN_EXACT), ("paper", lsm.LSM_GREEN_PAPER)])
+def test_apply_df_hform_parity(n, mode, green):
+    """The sampled-H form (Eq. 21 with the analytic H) in double-float arithmetic."""
+    med = sy.random_medium(n, h=8.0, seed=sum(n) + 5, frac=0.2)
+    h = handle(med, W, precision=lsm.LSM_MIXED, green=green, kernel=lsm.LSM_KERNEL_H)
+    u = field(med.shape, 14)
+    Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_apply_df(h, dev(u).reshape(-1), Au)
+    want = op.FFTOperator(med, W, mode=mode, form="h").apply(u)
+    got = host(Au).reshape(u.shape)
+    assert rel(got, want) < 1e-11
+    assert rel(u - got, u - want) < 1e-10
+
+
+def test_mixed_solve_hform_pair_residual():
+    """A batched mixed solve of the sampled-H form with the double-float residual against the
+    oracle's solution of the same form."""
+    med = sy.random_medium((12, 10, 9), h=10.0, seed=75, frac=0.1)
+    w = 2 * np.pi * 9.0
+    h = handle(med, w, precision=lsm.LSM_MIXED, tol=1e-8, kernel=lsm.LSM_KERNEL_H)
+    srcs = [(sy.explosion(), np.array([44.0, 41.0, 37.0])), (sy.double_couple_12(), np.array([31.0, 52.0, 45.0]))]
+    bs, xs_, want = [], [], []
+    F = op.FFTOperator(med, w, form="h")
+    for M, s in srcs:
+        b = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+        lsm.lsm_source(h, M, s, b)
+        bs.append(b)
+        xs_.append(torch.zeros_like(b))
+        u0 = host(b).reshape((3,) + med.shape)
+        xo, *_ = osv.bicgstab(F.apply, u0, tol=1e-12, maxit=400)
+        want.append(xo)
+    code, its, rrs, sts = lsm.lsm_solve_batched([h] * 2, bs, xs_)
+    assert code == lsm.LSM_OK
+    for x, xo, rr, b in zip(xs_, want, rrs, bs):
+        assert rr <= 1e-8
+        assert rel(host(x).reshape(xo.shape), xo) < 1e-6
+        u0 = host(b).reshape(xo.shape)
+        assert abs(osv.relres(F.apply, u0, host(x).reshape(xo.shape)) - rr) < 1e-9
+
+
 def test_apply_df_rejects_other_handles():
     med = sy.random_medium((8, 8, 8), h=10.0, seed=72, frac=0.1)
     u = dev(field(med.shape, 13)).reshape(-1)
     Au = torch.empty_like(u)
-    for kw in (dict(precision=lsm.LSM_FP64), dict(precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_FP64),
-               dict(precision=lsm.LSM_MIXED, kernel=lsm.LSM_KERNEL_H)):
+    for kw in (dict(precision=lsm.LSM_FP64), dict(precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_FP64)):
         h = handle(med, W, **kw)
         with pytest.raises(lsm.LSMError):
             lsm.lsm_apply_df(h, u, Au)
