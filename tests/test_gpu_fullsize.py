@@ -49,6 +49,12 @@ def test_apply_128_fp64_and_fp32_sampled(grf128):
     assert np.abs(_at(host(A32).astype(np.complex128), PTS) - want).max() < 2e-5 * scale
     # property at any size: FP32 and FP64 applies agree everywhere to FP32 accuracy
     assert np.linalg.norm(host(A32) - a64) / np.linalg.norm(a64) < 2e-5
+    # the mixed solver's double-float residual apply: oracle samples and agreement with FP64
+    Adf = torch.empty_like(ud)
+    lsm.lsm_apply_df(h, ud, Adf)
+    adf = host(Adf)
+    assert np.abs(_at(adf, PTS) - want).max() < 1e-11 * scale
+    assert np.linalg.norm(adf - a64) / np.linalg.norm(a64) < 1e-11
 
 
 def test_batched_mixed_solve_128(grf128):
