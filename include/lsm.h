@@ -92,12 +92,12 @@ typedef struct {
                           density), 24 spectra (18 H, 6 G), about 4x the spectrum memory.  The
                           adjoint calls (lsm_adjoint, lsm_solve_adjoint, lsm_gradient) and
                           lsm_apply_static return LSM_ERR_ARG for it. */
-    int residual;      /* LSM_MIXED: arithmetic of the outer residual's operator apply.  LSM_RESIDUAL_DFLOAT (default): double-float pairs
-                          (two FP32 words, about 48 significand bits, unit roundoff near
-                          2^-48; see lsm_apply_df) on the FP32 pipe, with the iterate scaled
-                          by a power of two to RMS(b) ~ 1 first; LSM_RESIDUAL_FP64: FP64.
-                          Adjoint solves always use FP64.  Ignored for LSM_FP64
-                          handles. */
+    int residual;      /* LSM_MIXED: arithmetic of the outer residual's operator apply.
+                          LSM_RESIDUAL_DFLOAT (default): double-float pairs (two FP32 words,
+                          about 48 significand bits, unit roundoff near 2^-48; see
+                          lsm_apply_df) on the FP32 pipe, with the iterate scaled by a power
+                          of two to RMS(b) ~ 1 first; LSM_RESIDUAL_FP64: FP64.  Adjoint
+                          solves always use FP64.  Ignored for LSM_FP64 handles. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */
