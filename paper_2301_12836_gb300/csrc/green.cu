@@ -221,10 +221,10 @@ __global__ void k_source(Dims d, GreenPar p, MomentSet ms, double sx, double sy,
                                   M[4] * g[0] + M[3] * g[1] + M[2] * g[2]};
             const double gMg = g[0] * Mg[0] + g[1] * Mg[1] + g[2] * Mg[2];
             const double tr = M[0] + M[1] + M[2];
-            for (int c = 0; c < 3; ++c) {
-                const double s1 = Mg[c], s2 = gMg * g[c], s3 = tr * g[c];
-                ms.u0[m][c * N + i] = make_double2(-(A.x * s1 + B.x * s2 + Cc.x * s3), -(A.y * s1 + B.y * s2 + Cc.y * s3));
-            }
+            // u0_c = -(A (M g)_c + (B g.M.g + C tr M) g_c): the g_c terms share one coefficient
+            const double2 D = make_double2(B.x * gMg + Cc.x * tr, B.y * gMg + Cc.y * tr);
+            for (int c = 0; c < 3; ++c)
+                ms.u0[m][c * N + i] = make_double2(-(A.x * Mg[c] + D.x * g[c]), -(A.y * Mg[c] + D.y * g[c]));
         }
     }
 }
