@@ -5,26 +5,33 @@ Workload (default "grf128_batched"): 128^3 grid, dx = 8 m, isotropic background
 (vp 3000, vs 1730 m/s, rho 2300 kg/m^3) plus a seeded Gaussian-random-field
 orthorhombic contrast (5% std, 40 m correlation; all 21 stiffness entries
 stored and processed), 32 frequencies 2-40 Hz x 8 random unit-norm moment
-tensors at the centre.  One step = the hot path for one frequency: the 8
-moment-tensor background fields (Eqs. 13-16) and one batched mixed-precision
-BiCGSTAB solve of the 8 systems (FP32 applies, FP64-accurate inner products,
-outer residual in double-float arithmetic (pairs of FP32 words, about 48
-significand bits) with FP64 storage, iterative refinement) to relative
-residual 1e-6.  Consecutive steps take
-consecutive frequencies.  The Green spectrum of each frequency is built before
-timing (it is set up once per frequency and shared by all its sources).
+tensors at the centre: 256 independent systems, solved to relative residual
+1e-6 with the mixed-precision BiCGSTAB (FP32 operator applies, FP64-accurate
+inner products and scalars, outer residual b - A x from an FP64 operator apply,
+iterative refinement in FP64 storage).
 
-value = LS operator applications (system-level matvecs, FP32 inner + outer residual) per second
-over the whole job; solves/s is reported beside it.
+The 256 systems run in memory waves: one wave = 8 consecutive frequencies x 8
+tensors = 64 systems in one batched solve (every kernel launch covers all 64).
+One step = one wave: its 64 moment-tensor background fields (Eqs. 13-16) and
+its batched solve.  Warm-up steps and timed steps both start at the first wave
+and cycle through the four, so K timed steps cover all 32 frequencies K/4 times
+each when K is a multiple of 4.  The Green spectrum of each frequency is built
+before timing (set up once per frequency, shared by its sources).
+
+value = LS operator applications (system-level matvecs: FP32 inner applies plus
+FP64 residual applies) per second over the whole job; solves/s beside it.
 """
 from __future__ import annotations
 
 import argparse
+import gc
 import json
+import math
 import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -37,35 +44,39 @@ METRIC = "LS matvecs/s and solves/s at 128³ (FP32+refine vs FP64), % of HBM roo
 STAGES = {0: "k_stress", 1: "k_divq+x fft", 2: "y fft", 3: "z fft+green", 4: "y ifft", 5: "x ifft+epilogue"}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=4, help="timed waves (a multiple of 4 covers every frequency equally)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grf128_batched")
     ap.add_argument("--grid", type=int, default=None, help="override the grid size (small profiling cases)")
+    ap.add_argument("--freqs", type=int, default=None, help="use only the first F frequencies (profiling cases)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--systems", type=int, default=8, help="moment tensors solved together per step")
+    ap.add_argument("--systems", type=int, default=8, help="moment tensors per frequency")
+    ap.add_argument("--wave-freqs", type=int, default=8, help="frequencies per memory wave (one batched solve)")
     ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
     ap.add_argument("--kernel", default="diff", choices=["diff", "h"],
                     help="operator form: difference form (default) or sampled analytic H (Eq. 21 literally)")
-    ap.add_argument("--residual", default="df", choices=["df", "fp64"],
-                    help="mixed: arithmetic of the outer residual's apply (double-float pairs or FP64)")
+    ap.add_argument("--residual", default="fp64", choices=["fp64", "df"],
+                    help="mixed: arithmetic of the outer residual's apply (FP64, or double-float pairs)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default FFT schedule (no autotuning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
-    ap.add_argument("--no-fp64-residual", action="store_true",
-                    help="skip the side measurement of the mixed solve with the FP64 residual apply")
+    ap.add_argument("--no-df-residual", action="store_true",
+                    help="skip the side measurement of the mixed solve with the double-float residual apply")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparator (context only)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # --------------------------------------------------------------------------------------------
-# algorithmic bytes of each apply stage, per system apply (b: bytes per complex, c: per real)
+# algorithmic bytes of each apply stage, per system apply (b: bytes per complex, c: per real;
+# share: systems of one launch that use the same Green spectrum, which the z pass stages once
+# per block for all of them)
 # --------------------------------------------------------------------------------------------
-def stage_bytes(stage, n, b, c):
+def stage_bytes(stage, n, b, c, share=1):
     nx, ny, nz = n
     N = nx * ny * nz
     Lx, Ly = 2 * nx, 2 * ny
@@ -76,13 +87,13 @@ def stage_bytes(stage, n, b, c):
         0: (3 * b + 21 * c + 6 * b) * N,
         1: 9 * N * b + N * c + 6 * E * b + 3 * ez * ey * Lx * b,
         2: 3 * ez * ey * Lx * b + 3 * ez * Ly * Lx * b,
-        3: 3 * ez * Ly * Lx * b + 6 * NO * b + 3 * nz * Ly * Lx * b,
+        3: 3 * ez * Ly * Lx * b + 6 * NO * b / share + 3 * nz * Ly * Lx * b,
         4: 3 * nz * Ly * Lx * b + 3 * nz * ny * Lx * b,
         5: 3 * nz * ny * Lx * b + 3 * N * b + 3 * N * b,
     }[stage]
 
 
-def stage_bytes_h(stage, n, b, c):
+def stage_bytes_h(stage, n, b, c, share=1):
     """Algorithmic bytes of the sampled-H form's stages (9 transformed planes, 24 spectra)."""
     nx, ny, nz = n
     N = nx * ny * nz
@@ -100,7 +111,6 @@ def stage_bytes_h(stage, n, b, c):
 
 
 def stage_flops_h(stage, n):
-    import math
     nx, ny, nz = n
     N = nx * ny * nz
     Lx, Ly, Lz = 2 * nx, 2 * ny, 2 * nz
@@ -118,7 +128,6 @@ def stage_flops_h(stage, n):
 def stage_flops(stage, n):
     """Model flops per system apply: 5 L log2 L per complex FFT line, 6 per complex multiply,
     2 per complex add, 4 per real-by-complex multiply-add."""
-    import math
     nx, ny, nz = n
     N = nx * ny * nz
     Lx, Ly, Lz = 2 * nx, 2 * ny, 2 * nz
@@ -150,25 +159,40 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profile(stage, precision, n):
-    """DRAM bytes per system apply of the timed stage from the committed ncu summary, if it matches."""
+def traffic_records():
+    """Records of profiles/roofline_traffic.txt: 'key: value' lines, a new record at each 'stage:'."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    recs = []
     if not os.path.exists(path):
-        return None
-    want_src = _csrc_digest()
-    rec = {}
+        return recs
     with open(path) as f:
         for line in f:
-            if ":" in line and not line.startswith("#"):
-                k, v = line.split(":", 1)
-                rec[k.strip()] = v.strip()
-    try:
-        if (int(rec["stage"]) != stage or rec["precision"] != precision or rec["csrc_sha256"] != want_src):
-            return None
-        scale = (n[0] * n[1] * n[2]) / float(rec["grid_voxels"])
-        return float(rec["dram_bytes_per_system_apply"]) * scale
-    except (KeyError, ValueError):
-        return None
+            if ":" not in line or line.startswith("#"):
+                continue
+            k, v = (x.strip() for x in line.split(":", 1))
+            if k == "stage":
+                recs.append({})
+            if recs:
+                recs[-1][k] = v
+    return recs
+
+
+def traffic_from_profile(stage, precision, n, share=None):
+    """DRAM bytes per system apply of a stage from the committed ncu summary, if one matches the
+    stage, the precision, the current kernel sources and (when the record names one) the number of
+    systems sharing a spectrum; scaled to grid n by its voxels."""
+    want_src = _csrc_digest()
+    for rec in traffic_records():
+        try:
+            if int(rec["stage"]) != stage or rec["precision"] != precision or rec["csrc_sha256"] != want_src:
+                continue
+            if share is not None and "share" in rec and int(rec["share"]) != share:
+                continue
+            scale = (n[0] * n[1] * n[2]) / float(rec["grid_voxels"])
+            return float(rec["dram_bytes_per_system_apply"]) * scale
+        except (KeyError, ValueError):
+            continue
+    return None
 
 
 def _csrc_digest():
@@ -193,10 +217,10 @@ class ClockSampler:
     def __init__(self, uuid=None):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="lsm_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
         if self.uuid:
             cmd += ["-i", self.uuid]
@@ -234,6 +258,10 @@ class ClockSampler:
                 for nm, v in zip(names, p[5:9]):
                     if v.lower().startswith("active"):
                         reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
@@ -241,12 +269,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------------------------
-# CPU baseline: the oracle as it stands, one operator apply of the same workload
+# CPU baseline: the oracle as it stands, operator applies of the same workload
 # --------------------------------------------------------------------------------------------
-def oracle_apply_sample(med, omega, reps=1):
+def oracle_apply_sample(med, omega, reps=1, workers=None):
+    """Time `reps` oracle applies (one thread: numpy.fft; workers = k: scipy.fft on k threads)."""
     from oracle import operator as op
     t0 = time.perf_counter()
-    F = op.FFTOperator(med, omega)
+    F = op.FFTOperator(med, omega, workers=workers)
     setup = time.perf_counter() - t0
     rng = np.random.default_rng(7)
     u = rng.standard_normal((3,) + med.shape) + 1j * rng.standard_normal((3,) + med.shape)
@@ -255,13 +284,25 @@ def oracle_apply_sample(med, omega, reps=1):
         t0 = time.perf_counter()
         F.apply(u)
         times.append(time.perf_counter() - t0)
-    return setup, times
+    return setup, times, F, u
 
 
-def rank_frequencies(rank, world, steps_total, nfreq):
-    """Frequencies (indices) a rank solves, one per step: ranks take disjoint consecutive blocks
-    (weak scaling: every rank does the same work; no data is exchanged between ranks)."""
-    return [(rank * steps_total + s) % nfreq for s in range(steps_total)]
+def freq_blocks(nfreq, per_wave):
+    """Consecutive frequency indices per memory wave."""
+    return [list(range(i, min(i + per_wave, nfreq))) for i in range(0, nfreq, per_wave)]
+
+
+def rank_blocks(rank, world, steps, nblocks):
+    """Wave (block) index of each step on one rank: every rank cycles through all the waves, rank r
+    starting at wave r, so all ranks do the same mix of work (weak scaling, replicas) and, while
+    world <= nblocks, work on different frequencies at any one step.  No data is exchanged."""
+    return [(rank + s) % nblocks for s in range(steps)]
+
+
+def rank_frequencies(rank, world, steps, nfreq, per_wave=1):
+    """Frequency indices a rank solves over `steps` waves (flattened)."""
+    blocks = freq_blocks(nfreq, per_wave)
+    return [f for b in rank_blocks(rank, world, steps, len(blocks)) for f in blocks[b]]
 
 
 def reduce_timing(ms, applies, solves, launches, world, dist=None, device="cpu"):
@@ -294,16 +335,17 @@ def workload_inputs(args):
         rng = np.random.default_rng(sy.BASE_SEED + 77)
         M = np.concatenate([M, sy.random_moment_tensors(args.systems - k, rng)])
         xs = np.repeat(xs[:1], args.systems, axis=0)
-    return wl, med, M[:args.systems], xs[:args.systems]
+    freqs = list(wl.freqs_hz)[:args.freqs] if args.freqs else list(wl.freqs_hz)
+    return wl, med, M[:args.systems], xs[:args.systems], freqs
 
 
 def run_reference(args, rank, world):
-    """The oracle, timed on the host cores: each step one LS apply of the workload."""
+    """The oracle, timed on the host cores: each step one LS apply of the workload (one thread)."""
     if rank != 0:
         return
-    wl, med, M, xs = workload_inputs(args)
-    omega = 2 * np.pi * wl.freqs_hz[0]
-    setup, times = oracle_apply_sample(med, omega, reps=args.warmup + args.steps)
+    wl, med, M, xs, freqs = workload_inputs(args)
+    omega = 2 * np.pi * freqs[0]
+    setup, times, _, _ = oracle_apply_sample(med, omega, reps=args.warmup + args.steps)
     timed = times[args.warmup:]
     T = sum(timed)
     value = len(timed) / T
@@ -311,7 +353,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(timed), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(args, wl, med),
+        "config": _config(args, wl, med, freqs),
         "cpu_baseline": {"value": value, "unit": "matvec/s", "cores": 1, "kind": "oracle",
                          "sample": f"one FP64 NumPy FFT apply of the {med.n[0]}^3 workload per step "
                                    f"(operator setup {setup:.1f} s untimed)"},
@@ -320,13 +362,137 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _config(args, wl, med):
-    f = wl.freqs_hz
+def _config(args, wl, med, freqs):
+    nb = len(freq_blocks(len(freqs), args.wave_freqs))
     return {"workload": wl.name if not args.grid else f"{wl.name}@{args.grid}", "grid": list(med.n), "dx_m": med.h,
-            "frequencies_hz": f"{f[0]:g}-{f[-1]:g} ({len(f)})", "systems_per_step": args.systems,
+            "frequencies_hz": f"{freqs[0]:g}-{freqs[-1]:g} ({len(freqs)})", "tensors_per_frequency": args.systems,
+            "systems": len(freqs) * args.systems,
+            "wave": {"systems": min(args.wave_freqs, len(freqs)) * args.systems,
+                     "frequencies": min(args.wave_freqs, len(freqs)), "waves": nb,
+                     "step": "one wave: its source fields and one batched solve of all its systems"},
+            "timed_passes_over_all_frequencies": round(args.steps / nb, 3),
             "precision": args.precision, "kernel": args.kernel, "tol": wl.tol, "parallelism": "replicas",
             "residual": args.residual if args.precision == "mixed" else None,
             "l2": "inputs larger than L2 (contrast, Green spectra and Krylov vectors exceed 126 MB)"}
+
+
+class Runner:
+    """Handles of one medium at every frequency, the wave buffers, and the step of the hot path."""
+
+    def __init__(self, lsm, torch, med, M, xs, freqs, blocks, nsys, opts, schedule=None):
+        self.lsm, self.torch = lsm, torch
+        self.M, self.xs = M, xs
+        self.freqs, self.blocks, self.nsys = freqs, blocks, nsys
+        dC = torch.from_numpy(med.dC).cuda().contiguous()
+        drho = torch.from_numpy(med.drho).cuda().contiguous()
+        self.handles = {}
+        self.base = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[0], opts)
+        self.handles[0] = self.base
+        for i in range(1, len(freqs)):
+            self.handles[i] = lsm.lsm_create_shared(self.base, 2 * np.pi * freqs[i])
+        del dC, drho
+        if schedule is not None:
+            lsm.lsm_set_schedule(self.base, lsm.LSM_FP64, schedule["fp64"])
+            if opts.precision == lsm.LSM_MIXED:
+                lsm.lsm_set_schedule(self.base, lsm.LSM_MIXED, schedule["fp32"])
+        self.N3 = 3 * self.base.N
+        self.wave = max(len(b) for b in blocks) * nsys
+        self.b = [torch.empty(self.N3, dtype=torch.complex128, device="cuda") for _ in range(self.wave)]
+        self.x = [torch.zeros(self.N3, dtype=torch.complex128, device="cuda") for _ in range(self.wave)]
+        self.same_xs = bool(np.all(xs == xs[:1]))
+        self.iters, self.relres = [], []
+
+    def launches(self):
+        return sum(self.lsm.lsm_launch_count(h) for h in self.handles.values())
+
+    def step(self, blk, xset=None):
+        lsm = self.lsm
+        xset = self.x if xset is None else xset
+        hs = []
+        for j, f in enumerate(self.blocks[blk]):
+            h = self.handles[f]
+            out = self.b[j * self.nsys:(j + 1) * self.nsys]
+            # moment tensors that share a position go through one source launch
+            if self.same_xs:
+                lsm.lsm_source_moments(h, self.M, self.xs[0], out)
+            else:
+                for k in range(self.nsys):
+                    lsm.lsm_source(h, self.M[k], self.xs[k], out[k])
+            hs += [h] * self.nsys
+        k = len(hs)
+        for v in xset[:k]:
+            v.zero_()
+        code, its, rrs, sts = lsm.lsm_solve_batched(hs, self.b[:k], xset[:k], check=False)
+        if code != lsm.LSM_OK:
+            raise RuntimeError(f"solve failed: {lsm.STATUS_NAMES.get(code)} {sts} relres {rrs}")
+        self.iters.extend(its)
+        self.relres.extend(rrs)
+        return k
+
+    def timed(self, seq):
+        """CUDA-event time (ms) of the steps seq on the current stream; returns (ms, solves)."""
+        torch = self.torch
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solves = 0
+        for blk in seq:
+            solves += self.step(blk)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), solves
+
+    def close(self):
+        self.handles.clear()
+        self.base = None
+        self.b = self.x = None
+        gc.collect()
+
+
+def stage_records(lsm, st_ms, st_launch, a64, a32, ms, n, kernel, pair, share):
+    """Per-stage rooflines: FP32 stages against HBM (algorithmic bytes), FP64 stages against the
+    FP64 pipe (model flops); double-float stages (FP32 pipe) against the HBM floor of their bytes
+    with their FP64-equivalent rate."""
+    peak, _ = peaks()
+    stages = []
+    for slot in range(12):
+        if st_launch[slot] == 0 or st_ms[slot] <= 0:
+            continue
+        f32 = slot >= 6
+        stage = slot % 6
+        napp = a32 if f32 else a64
+        if napp == 0:
+            continue
+        name = STAGES[stage] + ("<float>" if f32 else ("<dfloat>" if pair else "<double>"))
+        rec = {"kernel": name, "ms": round(st_ms[slot], 3), "launches": st_launch[slot],
+               "share_of_step": round(st_ms[slot] / ms, 4), "system_applies": napp}
+        sb, sf = (stage_bytes_h, stage_flops_h) if kernel == "h" else (stage_bytes, stage_flops)
+        if f32:
+            nbytes = sb(stage, n, 8, 4, share)
+            ach = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
+            rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": round(nbytes)})
+        elif pair:
+            fl = sf(stage, n)
+            nbytes = sb(stage, n, 16, 8, share)
+            gbs = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
+            rec.update({"bound": "alu (FP32 pipe, double-float)", "achieved": round(gbs, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(gbs / peak, 4), "algorithmic_bytes_per_system_apply": round(nbytes),
+                        "fp64_equivalent_tflops": round(fl * napp / (st_ms[slot] / 1e3) / 1e12, 4),
+                        "model_flops_per_system_apply": fl})
+        else:
+            fl = sf(stage, n)
+            ach = fl * napp / (st_ms[slot] / 1e3) / 1e12
+            nbytes = sb(stage, n, 16, 8, share)
+            rec.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                        "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                        "model_flops_per_system_apply": fl,
+                        "hbm_gbs": round(nbytes * napp / (st_ms[slot] / 1e3) / 1e9, 1),
+                        "algorithmic_bytes_per_system_apply": round(nbytes)})
+        stages.append(rec)
+    stages.sort(key=lambda r: -r["ms"])
+    return stages
 
 
 def main():
@@ -345,65 +511,37 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lsm.load()
-    wl, med, M, xs = workload_inputs(args)
+    wl, med, M, xs, freqs = workload_inputs(args)
     nsys = args.systems
     prec = lsm.LSM_MIXED if args.precision == "mixed" else lsm.LSM_FP64
-    steps_total = args.warmup + args.steps
-    freqs = list(wl.freqs_hz)
-    # weak scaling: rank r takes its own frequencies
-    fidx = rank_frequencies(rank, world, steps_total, len(freqs))
-    dC = torch.from_numpy(med.dC).cuda().contiguous()
-    drho = torch.from_numpy(med.drho).cuda().contiguous()
-    opts = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000,
-                                kernel=lsm.LSM_KERNEL_H if args.kernel == "h" else lsm.LSM_KERNEL_DIFF,
-                                residual=lsm.LSM_RESIDUAL_FP64 if args.residual == "fp64" else lsm.LSM_RESIDUAL_DFLOAT)
-    if args.inner_tol:
-        opts.inner_tol = args.inner_tol
-    handles = {}
+    pair = prec == lsm.LSM_MIXED and args.residual == "df"
+    blocks = freq_blocks(len(freqs), args.wave_freqs)
+    nb = len(blocks)
+    warm_seq = rank_blocks(rank, world, args.warmup, nb)
+    timed_seq = rank_blocks(rank, world, args.steps, nb)
+    kern = lsm.LSM_KERNEL_H if args.kernel == "h" else lsm.LSM_KERNEL_DIFF
+
+    def mk_opts(precision, residual):
+        o = lsm.lsm_default_opts(precision=precision, tol=wl.tol, maxit=2000, kernel=kern,
+                                 residual=lsm.LSM_RESIDUAL_DFLOAT if residual == "df" else lsm.LSM_RESIDUAL_FP64)
+        if args.inner_tol:
+            o.inner_tol = args.inner_tol
+        return o
+
     t_setup = time.perf_counter()
-    base = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[0]], opts)
-    handles[fidx[0]] = base
-    for i in fidx:
-        if i not in handles:
-            handles[i] = lsm.lsm_create_shared(base, 2 * np.pi * freqs[i])
-    del dC, drho
+    R = Runner(lsm, torch, med, M, xs, freqs, blocks, nsys, mk_opts(prec, args.residual))
     schedule = None
     if not args.no_tune:
-        v64, v32 = lsm.lsm_autotune(base, nsys, 2)
+        v64, v32 = lsm.lsm_autotune(R.base, nsys, 2)
         schedule = {"fp64": v64, "fp32": v32}
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
-    N3 = 3 * base.N
-    b = [torch.empty(N3, dtype=torch.complex128, device="cuda") for _ in range(nsys)]
-    x = [torch.zeros(N3, dtype=torch.complex128, device="cuda") for _ in range(nsys)]
-    stats = {"iters": [], "relres": []}
-    same_xs = bool(np.all(xs == xs[:1]))
 
-    def sources(h, out):
-        # moment tensors that share a position go through one source launch
-        if same_xs:
-            lsm.lsm_source_moments(h, M, xs[0], out)
-        else:
-            for j in range(nsys):
-                lsm.lsm_source(h, M[j], xs[j], out[j])
-
-    def step(s, xs_=None):
-        xs_ = x if xs_ is None else xs_
-        h = handles[fidx[s]]
-        sources(h, b)
-        for j in range(nsys):
-            xs_[j].zero_()
-        code, its, rrs, sts = lsm.lsm_solve_batched([h] * nsys, b, xs_, check=False)
-        if code != lsm.LSM_OK:
-            raise RuntimeError(f"solve failed: {lsm.STATUS_NAMES.get(code)} {sts} relres {rrs}")
-        stats["iters"].extend(its)
-        stats["relres"].extend(rrs)
-
-    for s in range(args.warmup):
-        step(s)
-    stats = {"iters": [], "relres": []}
-    launches0 = sum(lsm.lsm_launch_count(h) for h in handles.values())
-    lsm.lsm_timer_start(base, True)
+    for blk in warm_seq:
+        R.step(blk)
+    R.iters, R.relres = [], []
+    launches0 = R.launches()
+    lsm.lsm_timer_start(R.base, True)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
@@ -416,206 +554,94 @@ def main():
     torch.cuda.synchronize()
     with sampler:
         time.sleep(0.3)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for s in range(args.warmup, steps_total):
-            step(s)
-        e1.record()
-        torch.cuda.synchronize()
+        ms, solves = R.timed(timed_seq)
     if world > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    st_ms, st_launch, (a64, a32) = lsm.lsm_timer_read(base)
-    launches = sum(lsm.lsm_launch_count(h) for h in handles.values()) - launches0
-    solves = args.steps * nsys
+    st_ms, st_launch, (a64, a32) = lsm.lsm_timer_read(R.base)
+    launches = R.launches() - launches0
     applies = a64 + a32
     ms_max, applies_all, solves_all, launches_all = reduce_timing(ms, applies, solves, launches, world, dist, "cuda")
     value = applies_all / (ms_max / 1e3)
-    # per-stage rooflines: FP32 stages against HBM (algorithmic bytes), FP64 stages against the
-    # FP64 pipe (model flops); the dominant stage (largest share of the timed region) is reported.
-    # With the double-float residual (mixed) the FP64 slots time the pair apply:
-    # its model flops are those of the FP64 form, each carried out as several FP32 operations, so
-    # it is given against the HBM floor of its bytes and its FP64-equivalent rate, with no ALU frac.
-    pair = prec == lsm.LSM_MIXED and args.residual == "df"
-    peak, peak_kind = peaks()
-    stages = []
-    for slot in range(12):
-        if st_launch[slot] == 0 or st_ms[slot] <= 0:
-            continue
-        f32 = slot >= 6
-        stage = slot % 6
-        napp = a32 if f32 else a64
-        name = STAGES[stage] + ("<float>" if f32 else ("<dfloat>" if pair else "<double>"))
-        rec = {"kernel": name, "ms": round(st_ms[slot], 3), "launches": st_launch[slot],
-               "share_of_step": round(st_ms[slot] / ms, 4)}
-        sb, sf = (stage_bytes_h, stage_flops_h) if args.kernel == "h" else (stage_bytes, stage_flops)
-        if f32:
-            nbytes = sb(stage, med.n, 8, 4)
-            ach = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
-            rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": nbytes})
-        elif pair:
-            fl = sf(stage, med.n)
-            nbytes = sb(stage, med.n, 16, 8)
-            gbs = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
-            rec.update({"bound": "alu (FP32 pipe, double-float)", "achieved": round(gbs, 1), "peak": peak,
-                        "unit": "GB/s", "frac": round(gbs / peak, 4), "algorithmic_bytes_per_system_apply": nbytes,
-                        "fp64_equivalent_tflops": round(fl * napp / (st_ms[slot] / 1e3) / 1e12, 4),
-                        "model_flops_per_system_apply": fl})
-        else:
-            fl = sf(stage, med.n)
-            ach = fl * napp / (st_ms[slot] / 1e3) / 1e12
-            rec.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                        "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                        "model_flops_per_system_apply": fl})
-        stages.append(rec)
-    stages.sort(key=lambda r: -r["ms"])
+    stages = stage_records(lsm, st_ms, st_launch, a64, a32, ms, med.n, args.kernel, pair, nsys)
     dom = dict(stages[0]) if stages else {}
     if dom:
         prec_s = "mixed" if dom["kernel"].endswith("<float>") else ("dfloat" if dom["kernel"].endswith("<dfloat>") else "fp64")
         stage_id = [k for k, v in STAGES.items() if dom["kernel"].startswith(v)][0]
-        dom["traffic"] = traffic_from_profile(stage_id, prec_s, med.n) if args.kernel == "diff" else None
-        dom["peak_kind"] = peak_kind if dom["unit"] == "GB/s" else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"
-    roof = dom
-
+        dom["traffic"] = traffic_from_profile(stage_id, prec_s, med.n, nsys) if args.kernel == "diff" else None
+        dom["peak_kind"] = ("measured" if peaks()[1] == "measured" else "fallback") if dom["unit"] == "GB/s" else \
+            "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"
+    timed_freqs = sorted({f for blk in timed_seq for f in blocks[blk]})
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "matvec/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": ("f32+df64" if pair else "f32+f64") if prec == lsm.LSM_MIXED else "f64",
-        "data": "synthetic", "config": _config(args, wl, med),
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("f32+df64" if pair else "f32+f64") if prec == lsm.LSM_MIXED else "f64",
+        "data": "synthetic", "config": _config(args, wl, med, freqs),
+        "timed_frequencies": len(timed_freqs),
         "solves_per_s": round(solves_all / (ms_max / 1e3), 4),
         "matvecs": {"fp32": a32, "residual": a64, "residual_arith": "df64" if pair else "f64",
-                    "per_solve": round(applies / solves, 2)},
-        "iterations_mean": round(float(np.mean(stats["iters"])), 2),
-        "relres_max": float(np.max(stats["relres"])),
+                    "per_solve": round(applies / solves, 2), "residual_per_solve": round(a64 / solves, 3)},
+        "iterations_mean": round(float(np.mean(R.iters)), 2),
+        "relres_max": float(np.max(R.relres)),
         "setup_s": round(t_setup, 2),
         "schedule": schedule,
-        "roofline": roof, "stages": stages, "gpu_launches": int(launches_all),
+        "roofline": dom, "stages": stages, "gpu_launches": int(launches_all),
     }
     cs = sampler.summary()
     if cs:
         line["clocks"] = cs
 
-    # end to end through the C ABI with host buffers: every step's solutions are copied to pinned
+    # end to end through the C ABI with host buffers: every wave's solutions are copied to pinned
     # host memory inside the timed region.  Two solution sets alternate, and each set's copy runs
-    # on a copy stream while the next step solves into the other set; a set is reused only after
+    # on a copy stream while the next wave solves into the other set; a set is reused only after
     # its copy has finished.
     if not args.no_e2e:
-        host = [[torch.empty(N3, dtype=torch.complex128, pin_memory=True) for _ in range(nsys)] for _ in range(2)]
-        xsets = [x, [torch.zeros_like(v) for v in x]]
+        host = [[torch.empty(R.N3, dtype=torch.complex128, pin_memory=True) for _ in range(R.wave)] for _ in range(2)]
+        xsets = [R.x, [torch.zeros_like(v) for v in R.x]]
         copy_stream = torch.cuda.Stream()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
-        lsm.lsm_timer_start(base, False)
+        lsm.lsm_timer_start(R.base, False)
         # one untimed copy into every pinned buffer: the first transfers into freshly pinned pages
-        # measured slow while kernels ran beside them (on a box that had run other GPU jobs)
+        # measured slow while kernels ran beside them
         with torch.cuda.stream(copy_stream):
             for k in range(2):
-                for j in range(nsys):
+                for j in range(R.wave):
                     host[k][j].copy_(xsets[k][j], non_blocking=True)
         copy_stream.synchronize()
-        # one untimed step: the solver's iteration graph is captured per timer state, so the first
-        # solve after switching the stage timer off re-captures it
-        step(args.warmup, xsets[1])
-        lsm.lsm_timer_start(base, False)   # same timer state; zeroes the apply counters
+        # one untimed step: the solver's iteration graph is captured per stage-timer state
+        R.step(timed_seq[0], xsets[1])
+        lsm.lsm_timer_start(R.base, False)   # same timer state; zeroes the apply counters
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i, s in enumerate(range(args.warmup, steps_total)):
+        e_solves = 0
+        d2h = 0
+        for i, blk in enumerate(timed_seq):
             k = i % 2
             cur = torch.cuda.current_stream()
             cur.wait_event(copied[k])
-            step(s, xsets[k])
+            ns = R.step(blk, xsets[k])
+            e_solves += ns
+            d2h += ns * R.N3 * 16
             solved = torch.cuda.Event()
             solved.record(cur)
             copy_stream.wait_event(solved)
             with torch.cuda.stream(copy_stream):
-                for j in range(nsys):
+                for j in range(ns):
                     host[k][j].copy_(xsets[k][j], non_blocking=True)
             copied[k].record(copy_stream)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        _, _, (e64, e32) = lsm.lsm_timer_read(base)
+        _, _, (e64, e32) = lsm.lsm_timer_read(R.base)
         line["e2e"] = {"value": round((e64 + e32) / te, 3), "unit": "matvec/s",
-                       "h2d_bytes_per_step": nsys * 9 * 8, "d2h_bytes_per_step": nsys * N3 * 16,
-                       "solves_per_s": round(solves / te, 4)}
-
-    # the same K steps with the mixed solve's residual apply in FP64 (LSM_RESIDUAL_FP64), timed the
-    # same way (CUDA events, one untimed step first), beside the double-float headline
-    if pair and not args.no_fp64_residual and rank == 0:
-        dC = torch.from_numpy(med.dC).cuda().contiguous()
-        drho = torch.from_numpy(med.drho).cuda().contiguous()
-        o_r = lsm.lsm_default_opts(precision=prec, tol=wl.tol, maxit=2000, kernel=opts.kernel,
-                                   residual=lsm.LSM_RESIDUAL_FP64)
-        hr = {fidx[args.warmup]: lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho,
-                                                2 * np.pi * freqs[fidx[args.warmup]], o_r)}
-        del dC, drho
-        rbase = hr[fidx[args.warmup]]
-        for s in range(args.warmup, steps_total):
-            if fidx[s] not in hr:
-                hr[fidx[s]] = lsm.lsm_create_shared(rbase, 2 * np.pi * freqs[fidx[s]])
-        if schedule is not None:
-            lsm.lsm_set_schedule(rbase, lsm.LSM_FP64, schedule["fp64"])
-            lsm.lsm_set_schedule(rbase, lsm.LSM_MIXED, schedule["fp32"])
-        rr_max = []
-
-        def rstep(s):
-            h = hr[fidx[s]]
-            sources(h, b)
-            for j in range(nsys):
-                x[j].zero_()
-            code, its, rrs, sts = lsm.lsm_solve_batched([h] * nsys, b, x, check=False)
-            if code != lsm.LSM_OK:
-                raise RuntimeError(f"FP64-residual solve failed: {lsm.STATUS_NAMES.get(code)} {sts}")
-            rr_max.append(max(rrs))
-
-        rstep(args.warmup)
-        lsm.lsm_timer_start(rbase, False)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for s in range(args.warmup, steps_total):
-            rstep(s)
-        e1.record()
-        torch.cuda.synchronize()
-        tr = e0.elapsed_time(e1) / 1e3
-        _, _, (r64, r32) = lsm.lsm_timer_read(rbase)
-        line["fp64_residual"] = {"value": round((r64 + r32) / tr, 3), "unit": "matvec/s",
-                                 "solves_per_s": round(solves / tr, 4), "ms_per_step": round(tr * 1e3 / args.steps, 3),
-                                 "dtype": "f32+f64", "relres_max": float(np.max(rr_max[1:])),
-                                 "note": "the mixed solve with its outer residual apply in FP64; same steps, "
-                                         "timed with CUDA events"}
-        del hr, rbase
-
-    # the plain FP64 GPU form on the first frequency, for the precision comparison
-    if prec == lsm.LSM_MIXED and not args.no_fp64_form and rank == 0:
-        dC = torch.from_numpy(med.dC).cuda().contiguous()
-        drho = torch.from_numpy(med.drho).cuda().contiguous()
-        o64 = lsm.lsm_default_opts(precision=lsm.LSM_FP64, tol=wl.tol, maxit=2000, kernel=opts.kernel)
-        h64 = lsm.lsm_create(med.n, med.h, med.lam0, med.mu0, med.rho0, dC, drho, 2 * np.pi * freqs[fidx[-1]], o64)
-        del dC, drho
-        if schedule is not None:
-            lsm.lsm_set_schedule(h64, lsm.LSM_FP64, schedule["fp64"])
-        sources(h64, b)
-        for j in range(nsys):
-            x[j].zero_()
-        lsm.lsm_timer_start(h64, False)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        code, its, rrs, sts = lsm.lsm_solve_batched([h64] * nsys, b, x, check=False)
-        torch.cuda.synchronize()
-        tf = time.perf_counter() - t0
-        _, _, (f64, _) = lsm.lsm_timer_read(h64)
-        line["fp64_form"] = {"solves_per_s": round(nsys / tf, 4), "matvecs_per_s": round(f64 / tf, 3),
-                             "iterations_mean": float(np.mean(its)), "relres_max": float(np.max(rrs)),
-                             "status": lsm.STATUS_NAMES.get(code), "frequency_hz": freqs[fidx[-1]]}
-        del h64
+                       "h2d_bytes_per_step": R.wave * 9 * 8, "d2h_bytes_per_step": round(d2h / len(timed_seq)),
+                       "solves_per_s": round(e_solves / te, 4)}
+        del host, xsets, copy_stream
 
     # context, outside the timed region: cuFFT (through torch.fft) doing only the forward and
     # inverse 3-D transforms of the three padded components of one FP32 apply (no pruning, no
     # contraction, no Green multiply), against this library's FFT stages 1-5 of the same apply
     # (which also form the divergence, skip the padding, multiply by the spectrum and crop)
-    if rank == 0 and not args.no_cufft and args.kernel == "diff":
+    if rank == 0 and not args.no_cufft and args.kernel == "diff" and a32:
         L = [2 * v for v in med.n]
         buf = torch.zeros((3, L[2], L[1], L[0]), dtype=torch.complex64, device="cuda")
         for _ in range(2):
@@ -630,18 +656,69 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         del buf
-        ours = sum(st_ms[6 + k] for k in range(1, 6)) / a32 if a32 else None
+        ours = sum(st_ms[6 + k] for k in range(1, 6)) / a32
         line["cufft_comparator"] = {
             "cufft_fft_ifft_ms_per_system_apply": round(e0.elapsed_time(e1) / reps, 4),
-            "ours_stages_1_5_ms_per_system_apply": round(ours, 4) if ours else None,
+            "ours_stages_1_5_ms_per_system_apply": round(ours, 4),
             "note": "complex64, 3 components, full (2n)^3 transforms vs pruned two-step passes with the "
                     "divergence, Green multiply and crop fused in; not part of the timed region"}
+    R.close()
+    torch.cuda.empty_cache()
+    one_pass = list(range(nb))
+
+    # side line: the same systems with the residual apply in double-float pairs (or in FP64 when
+    # the headline used pairs), one pass over every wave after one untimed wave
+    if prec == lsm.LSM_MIXED and not args.no_df_residual and rank == 0:
+        other = "fp64" if pair else "df"
+        S = Runner(lsm, torch, med, M, xs, freqs, blocks, nsys, mk_opts(prec, other), schedule)
+        S.step(one_pass[0])
+        S.iters, S.relres = [], []
+        lsm.lsm_timer_start(S.base, False)
+        tr, ns = S.timed(one_pass)
+        _, _, (r64, r32) = lsm.lsm_timer_read(S.base)
+        key = "fp64_residual" if other == "fp64" else "df_residual"
+        line[key] = {"value": round((r64 + r32) / (tr / 1e3), 3), "unit": "matvec/s",
+                     "solves_per_s": round(ns / (tr / 1e3), 4), "ms_per_step": round(tr / len(one_pass), 3),
+                     "dtype": "f32+f64" if other == "fp64" else "f32+df64", "steps": len(one_pass),
+                     "relres_max": float(np.max(S.relres)), "iterations_mean": round(float(np.mean(S.iters)), 2),
+                     "residual_matvecs_per_solve": round(r64 / ns, 3),
+                     "note": "the mixed solve with its outer residual apply in "
+                             + ("FP64" if other == "fp64" else "double-float pairs (about 48 significand bits)")
+                             + "; the same 256 systems, one pass, CUDA-event timed"}
+        S.close()
+        torch.cuda.empty_cache()
+
+    # the plain FP64 GPU form on the same systems (all waves, one pass), for the precision
+    # comparison at the same relative residual
+    if prec == lsm.LSM_MIXED and not args.no_fp64_form and rank == 0:
+        P = Runner(lsm, torch, med, M, xs, freqs, blocks, nsys, mk_opts(lsm.LSM_FP64, "fp64"), schedule)
+        P.step(one_pass[0])
+        P.iters, P.relres = [], []
+        lsm.lsm_timer_start(P.base, False)
+        tf, ns = P.timed(one_pass)
+        _, _, (f64, _) = lsm.lsm_timer_read(P.base)
+        line["fp64_form"] = {"solves_per_s": round(ns / (tf / 1e3), 4), "matvecs_per_s": round(f64 / (tf / 1e3), 3),
+                             "ms_per_step": round(tf / len(one_pass), 3), "steps": len(one_pass), "solves": ns,
+                             "iterations_mean": round(float(np.mean(P.iters)), 2),
+                             "relres_max": float(np.max(P.relres)),
+                             "note": "plain FP64 BiCGSTAB on the same systems (every frequency and tensor), "
+                                     "one pass, CUDA-event timed"}
+        P.close()
+        torch.cuda.empty_cache()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        setup, times = oracle_apply_sample(med, 2 * np.pi * freqs[fidx[0]], reps=1)
+        setup, times, F, u = oracle_apply_sample(med, 2 * np.pi * freqs[0], reps=1)
+        ncores = os.cpu_count() or 1
+        F.workers = ncores
+        t0 = time.perf_counter()
+        F.apply(u)
+        t_all = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": round(1.0 / times[0], 5), "unit": "matvec/s", "cores": 1, "kind": "oracle",
                                 "sample": f"one FP64 NumPy FFT apply of the {med.n[0]}^3 workload "
-                                          f"({times[0]:.1f} s; operator setup {setup:.1f} s untimed)"}
+                                          f"({times[0]:.1f} s; operator setup {setup:.1f} s untimed)",
+                                "all_cores": {"value": round(1.0 / t_all, 5), "unit": "matvec/s", "cores": ncores,
+                                              "sample": f"the same apply with scipy.fft on {ncores} threads "
+                                                        f"({t_all:.1f} s; the rest of the oracle is single-threaded)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -275,6 +275,36 @@ lsm_status lsm_source_gradient(lsm_t h, const double xs[3], const void *lam, dou
 lsm_status lsm_time_traces(int nf, double df, int ntr, const void *spectra, int nt, double dt, double fp, double t0,
                            double *traces, void *stream);
 
+/*
+ * Receiver seismograms of one moment-tensor source, the whole chain of Sec. 4.1.2: for each
+ * frequency f_k = k df, k = 1 .. nf-1, the background field (Eqs. 13-16) and the LS solution of
+ * A_k u_k = u0_k (BiCGSTAB to the handle's tolerance, Eq. 22), the three displacement components
+ * read at the receiver nodes, then the time traces of lsm_time_traces (k = 0 contributes nothing:
+ * the Ricker weight vanishes at f = 0).  The frequencies are solved in waves of up to `wave`
+ * systems, each wave one lsm_solve_batched over handles created with lsm_create_shared.
+ *   base     handle of the medium; its options (precision, tolerance, operator form, taper) are
+ *            used, its own frequency is not
+ *   nf, df   2 <= nf <= 12288 frequencies f_k = k df [Hz], df > 0
+ *   M, xs    host double[6] moment tensor (Voigt, as lsm_source), host double[3] position [m]
+ *   nrec     number of receivers (>= 1);  rec  host int[3 * nrec]: node indices (ix, iy, iz) of
+ *            receiver r at rec[3r .. 3r+2], each inside the grid
+ *   nt, dt, fp, t0  samples, interval [s], Ricker peak frequency [Hz] and delay [s], as in
+ *            lsm_time_traces
+ *   traces   device float64 [nrec][3][nt] (written when the call returns LSM_OK or
+ *            LSM_WARN_SOURCE_ON_NODE): trace 3 r + c is component c at receiver r
+ *   wave     1 .. 256 systems per batched solve
+ *   iters, relres  host int[nf] / double[nf] or NULL: per frequency as lsm_solve reports them
+ *            (entry 0 is 0)
+ * Allocates, for the duration of the call, the [nf][3 nrec] receiver spectra and per wave the
+ * handles' Green spectra and two fields per frequency; the base handle's solver workspace grows to
+ * `wave` systems and stays.  Returns the first failing status of a solve (traces not written),
+ * LSM_WARN_SOURCE_ON_NODE if a node coincides with the source (u0 = 0 there), else LSM_OK.
+ * Synchronises the stream.
+ */
+lsm_status lsm_seismograms(lsm_t base, int nf, double df, const double M[6], const double xs[3], int nrec,
+                           const int *rec, int nt, double dt, double fp, double t0, double *traces, int wave,
+                           int *iters, double *relres);
+
 /* Number of kernel launches the library has issued on this handle (diagnostics). */
 long long lsm_launch_count(lsm_t h);
 
@@ -336,16 +366,18 @@ lsm_status lsm_timer_start(lsm_t h, int enable);
 lsm_status lsm_timer_read(lsm_t h, double ms[12], long long launches[12], long long applies[2]);
 
 /*
- * FP64 operator apply that allocates nothing (the paper has no counterpart; this is a service
- * to callers that cannot call cudaMalloc when they apply the operator: code running while its
- * stream is captured into a CUDA graph, serving loops whose device memory is reserved up front
- * by another allocator, latency-critical loops that must not meet an out-of-memory error).
- * Same result as lsm_apply; the handle itself must already exist (lsm_create allocates).
+ * FP64 operator apply that allocates nothing (the paper has no counterpart).  It serves callers
+ * that cannot call cudaMalloc when they apply the operator: a process whose device memory was
+ * reserved up front by another allocator (for instance a serving framework whose caching
+ * allocator holds the device), or a loop that must not stop halfway on an out-of-memory error or
+ * on the device-wide synchronisation cudaMalloc may bring.  Same result as lsm_apply; the handle
+ * itself must already exist (lsm_create allocates).
  *   u, Au  device complex128, 3 * nz*ny*nx; u != Au.
  * The workspace is one library-wide array in device global memory of 64 MiB, present on every
- * GPU that loads the library until the process exits.  A grid needs about
- * 384 * nx * ny * (nz + 1) bytes of it (cubic grids up to 54^3 fit); a grid that needs more is
- * rejected with LSM_ERR_ARG.  The first call on each device looks up the array's device address
+ * GPU that loads the library until the process exits.  A grid needs 384 * nx * ny * (nz + 2)
+ * bytes of it plus 256 (the largest cubic grid the library accepts that fits is 54^3); a grid
+ * that needs more is rejected with LSM_ERR_ARG, and so is a call made while another device than
+ * the handle's is current.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls share
  * the one array and each call leaves its contents behind; nothing in it needs to start at zero.
  * Calls whose work overlaps on the GPU (different streams, or different handles without

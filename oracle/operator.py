@@ -170,11 +170,16 @@ class FFTOperator:
     sigma-hat = FFT(pad sigma), w-hat = FFT(pad(drho u)),
     q-hat_j = sum_k i kappa_k sigma-hat_jk + w^2 w-hat_j,
     u_s = crop IFFT(T-hat q-hat), A u = u - u_s.
+
+    workers: None (default) transforms with numpy.fft on one thread; an integer k transforms
+    with scipy.fft on k threads (the same discrete Fourier transform; used to time the oracle on
+    all of a machine's cores).  It may be changed after construction.
     """
 
-    def __init__(self, medium, omega, mode="exact", form="fd"):
+    def __init__(self, medium, omega, mode="exact", form="fd", workers=None):
         if form not in ("fd", "h"):
             raise ValueError(form)
+        self.workers = workers
         self.m = medium
         self.omega = float(omega)
         self.n = medium.n
@@ -194,6 +199,18 @@ class FFTOperator:
         # kappa as broadcastable arrays over (z, y, x)
         self.kappa = (kap[0][None, None, :], kap[1][None, :, None], kap[2][:, None, None])
 
+    def _fftn(self, a):
+        if self.workers is None:
+            return np.fft.fftn(a, axes=(-3, -2, -1))
+        import scipy.fft
+        return scipy.fft.fftn(a, axes=(-3, -2, -1), workers=self.workers)
+
+    def _ifftn(self, a):
+        if self.workers is None:
+            return np.fft.ifftn(a, axes=(-3, -2, -1))
+        import scipy.fft
+        return scipy.fft.ifftn(a, axes=(-3, -2, -1), workers=self.workers)
+
     def _pad(self, f):
         nx, ny, nz = self.n
         F = np.zeros(f.shape[:-3] + self.P, dtype=np.complex128)
@@ -207,19 +224,19 @@ class FFTOperator:
     def scattered(self, u):
         m = self.m
         sig = stress(m.dC, strain(u, m.h))
-        sh = np.fft.fftn(self._pad(sig), axes=(-3, -2, -1))
-        wh = np.fft.fftn(self._pad(m.drho * u), axes=(-3, -2, -1))
+        sh = self._fftn(self._pad(sig))
+        wh = self._fftn(self._pad(m.drho * u))
         if self.form == "h":
             # Eq. 21: u-hat_i = sum_J H-hat_iJ sigma-hat_J + w^2 sum_j T-hat_ij w-hat_j
             uh = (np.einsum("iJ...,J...->i...", self.Hhat, sh)
                   + self.omega ** 2 * np.einsum("ij...,j...->i...", self.That, wh))
-            return self._crop(np.fft.ifftn(uh, axes=(-3, -2, -1)))
+            return self._crop(self._ifftn(uh))
         qh = self.omega ** 2 * wh
         for j in range(3):
             for k in range(3):
                 qh[j] = qh[j] + 1j * self.kappa[k] * sh[T2V[j][k]]
         uh = np.einsum("ij...,j...->i...", self.That, qh)
-        return self._crop(np.fft.ifftn(uh, axes=(-3, -2, -1)))
+        return self._crop(self._ifftn(uh))
 
     def apply(self, u):
         return u - self.scattered(u)

@@ -34,3 +34,28 @@ def traces(spectra, df, nt, dt, fp, t0):
     S = (wgt * W)[:, None] * ph                                 # (K+1, nt)
     out = np.tensordot(spectra, S, axes=([0], [0]))            # (..., nt) complex
     return df * np.real(out)
+
+
+def seismograms(medium, nf, df, M, xs, receivers, nt, dt, fp, t0, mode="exact", tol=1e-12, maxit=1000):
+    """The whole chain of Sec. 4.1.2 for one moment-tensor source: for f_k = k df, k = 1 .. nf-1,
+    solve the LS system A_k u_k = u0_k (Eqs. 13-16, 21, 22) with the oracle's BiCGSTAB, read the
+    three displacement components at the receiver nodes, and synthesise the traces above.  The
+    k = 0 row stays zero (the Ricker weight W_0 is zero).
+
+    receivers: (nrec, 3) integer node indices (ix, iy, iz).  Returns (traces (nrec, 3, nt),
+    spectra (nf, nrec, 3), iterations per frequency)."""
+    from . import operator as _op, solver as _solver, source as _source
+    rec = np.asarray(receivers, dtype=int)
+    U = np.zeros((nf, rec.shape[0], 3), dtype=np.complex128)
+    iters = [0] * nf
+    for k in range(1, nf):
+        w = 2.0 * np.pi * k * df
+        F = _op.FFTOperator(medium, w, mode)
+        u0, _ = _source.background_field(medium.n, medium.h, M, xs, w, medium.lam0, medium.mu0, medium.rho0, mode)
+        u, it, _, status, _ = _solver.bicgstab(F.apply, u0, tol=tol, maxit=maxit)
+        if status != _solver.OK:
+            raise RuntimeError(f"oracle solve at {k * df} Hz did not converge")
+        iters[k] = it
+        for r, (ix, iy, iz) in enumerate(rec):
+            U[k, r, :] = u[:, iz, iy, ix]
+    return traces(U, df, nt, dt, fp, t0), U, iters

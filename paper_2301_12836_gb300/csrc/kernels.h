@@ -94,6 +94,10 @@ cudaError_t launch_taper(const Dims& d, int width, double* dC, double* drho, cud
 cudaError_t launch_time_traces(int nf, double df, int ntr, const double2* U, int nt, double dt, double fp, double t0,
                                double* out, cudaStream_t st);
 
+// Receiver gather for the seismogram chain: out[r * 3 + c] = u[c * N + node[r]], r < nrec (FP64).
+cudaError_t launch_gather_receivers(const double2* u, long long N, const long long* node, int nrec, double2* out,
+                                    cudaStream_t st);
+
 // Precision converters.  d2df: n reals to double-float pairs; df2d_inplace: n double-float pairs
 // to doubles in the same memory (8 bytes each).
 cudaError_t launch_d2df(const double* in, dfloat* out, long long n, cudaStream_t st, long long* nlaunch);

@@ -73,6 +73,7 @@ struct Store {
     int kernel = LSM_KERNEL_DIFF;
     int sched[2][6] = {{0}};   // FFT schedule variant per apply stage, [FP64, FP32]
     cudaStream_t st = nullptr;
+    int device = 0;            // CUDA device current at lsm_create (the handle's memory lives there)
     double* dC64 = nullptr;
     double* drho64 = nullptr;
     float* dC32 = nullptr;
@@ -294,6 +295,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     Store* s = new Store();
     h->s = s;
     s->st = (cudaStream_t)stream;
+    if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
     s->precision = o.precision;
     s->green = o.green;
     s->pair = o.precision == LSM_MIXED && o.residual == LSM_RESIDUAL_DFLOAT;
@@ -1228,10 +1230,9 @@ extern "C" lsm_status lsm_timer_read(lsm_t h, double ms[12], long long launches[
 // Operator apply without any device allocation.
 //
 // lsm_apply allocates its FP64 workspace with cudaMalloc on a handle's first apply.  Some callers
-// cannot allocate at that point: code running while a stream is being captured into a CUDA graph
-// (device allocation is not a capturable operation), serving loops that have reserved all device
-// memory up front through another allocator and forbid further cudaMalloc calls, or callers that
-// must not risk an out-of-memory failure in the middle of a time-critical loop.
+// cannot allocate at that point: a serving process whose device memory was reserved up front by
+// another allocator (a framework's caching allocator holding the whole device), or a loop that must
+// not stop on an out-of-memory error, or on cudaMalloc's implicit synchronisation, halfway through.
 // lsm_apply_static gives them the same FP64 apply with its workspace taken from one library-wide
 // array in device global memory (g_static_scratch, STATIC_SCRATCH_BYTES per device that loads the
 // library, held until the process exits).
@@ -1245,17 +1246,14 @@ constexpr int MAX_DEVICES = 64;
 void* g_static_addr[MAX_DEVICES] = {nullptr};
 std::mutex g_static_mu;
 
-// Device address of g_static_scratch on the current device; looked up once per device (the
-// host-side symbol is only a stand-in and must never be handed to a kernel).
-cudaError_t static_scratch_addr(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// Device address of g_static_scratch on device dev, which must be current; looked up once per
+// device (the host-side symbol is only a stand-in and must never be handed to a kernel).
+cudaError_t static_scratch_addr(int dev, void** out) {
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_addr[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
         g_static_addr[dev] = p;
     }
@@ -1263,37 +1261,38 @@ cudaError_t static_scratch_addr(void** out) {
     return cudaSuccess;
 }
 
-}  // namespace
+// The argument block reaches the device as a kernel parameter (copied when the launch is made),
+// so no host buffer has to outlive the call.
+__global__ void k_put_apply_args(ApplySys<double>* dst, ApplySys<double> a) { *dst = a; }
 
-// bytes of the static array one apply on an n[0] x n[1] x n[2] grid uses
-static size_t static_apply_bytes(const int n[3]) {
-    Dims d;
-    d.nx = n[0]; d.ny = n[1]; d.nz = n[2];
-    d.Lx = 2 * d.nx; d.Ly = 2 * d.ny; d.Lz = 2 * d.nz;
-    d.ex = d.nx + 2; d.ey = d.ny + 2; d.ez = d.nz + 2;
-    d.N = (long long)d.nx * d.ny * d.nz;
-    long long e1, e2;
-    apply_ws_elems(d, LSM_KERNEL_DIFF, &e1, &e2);
-    return align_up(sizeof(ApplySys<double>)) + align_up(e1 * sizeof(double2)) + align_up(e2 * sizeof(double2));
+// bytes of the static array one apply with the handle's geometry uses: the argument block and the
+// two workspaces the apply itself sizes with apply_ws_elems
+size_t static_apply_bytes(const Store* s, long long* e1, long long* e2) {
+    apply_ws_elems(s->d, s->kernel, e1, e2);
+    return align_up(sizeof(ApplySys<double>)) + align_up(*e1 * sizeof(double2)) + align_up(*e2 * sizeof(double2));
 }
+
+}  // namespace
 
 extern "C" lsm_status lsm_apply_static(lsm_t h, const void* u, void* Au) {
     if (!h) return fail(nullptr, LSM_ERR_ARG, "lsm_apply_static: null handle");
     if (!u || !Au || u == Au) return fail(h, LSM_ERR_ARG, "lsm_apply_static: u and Au must be distinct non-null device buffers");
     Store* s = h->s;
     if (s->kernel == LSM_KERNEL_H) return fail(h, LSM_ERR_ARG, "lsm_apply_static: not available for LSM_KERNEL_H");
-    const int n[3] = {s->d.nx, s->d.ny, s->d.nz};
-    const size_t need = static_apply_bytes(n);
+    int cur = -1;
+    CK(h, cudaGetDevice(&cur));
+    if (cur != s->device)
+        return fail(h, LSM_ERR_ARG, "lsm_apply_static: the handle's device must be the current device");
+    long long e1, e2;
+    const size_t need = static_apply_bytes(s, &e1, &e2);
     if (need > STATIC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof(msg), "lsm_apply_static: grid %dx%dx%d needs %zu bytes of scratch, more than the %zu-byte static array",
-                 n[0], n[1], n[2], need, (size_t)STATIC_SCRATCH_BYTES);
+                 s->d.nx, s->d.ny, s->d.nz, need, (size_t)STATIC_SCRATCH_BYTES);
         return fail(h, LSM_ERR_ARG, msg);
     }
     void* base = nullptr;
-    CK(h, static_scratch_addr(&base));
-    long long e1, e2;
-    apply_ws_elems(s->d, s->kernel, &e1, &e2);
+    CK(h, static_scratch_addr(cur, &base));
     char* p = (char*)base;
     ApplySys<double>* dev_args = (ApplySys<double>*)p;
     double2* w1 = (double2*)(p + align_up(sizeof(ApplySys<double>)));
@@ -1309,7 +1308,9 @@ extern "C" lsm_status lsm_apply_static(lsm_t h, const void* u, void* Au) {
     a.omega2 = h->omega * h->omega;
     a.run = nullptr;
     a.count = nullptr;
-    CK(h, cudaMemcpyAsync(dev_args, &a, sizeof(a), cudaMemcpyHostToDevice, s->st));
+    k_put_apply_args<<<1, 1, 0, s->st>>>(dev_args, a);
+    CK(h, cudaGetLastError());
+    h->nl += 1;
     Medium m = medium_of(s, 0);
     m.timer = nullptr;
     cudaError_t e = launch_apply<double>(m, s->pl64, dev_args, 1, s->st, &h->nl);
@@ -1325,4 +1326,101 @@ extern "C" lsm_status lsm_time_traces(int nf, double df, int ntr, const void* sp
     cudaError_t e = launch_time_traces(nf, df, ntr, (const double2*)spectra, nt, dt, fp, t0, traces, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lsm_time_traces");
     return LSM_OK;
+}
+
+// Seismogram chain (Sec. 4.1.2): LS solves at f_k = k df wave by wave, receiver gather, traces.
+extern "C" lsm_status lsm_seismograms(lsm_t base, int nf, double df, const double M[6], const double xs[3], int nrec,
+                                      const int* rec, int nt, double dt, double fp, double t0, double* traces, int wave,
+                                      int* iters, double* relres) {
+    if (!base) return fail(nullptr, LSM_ERR_ARG, "lsm_seismograms: null handle");
+    if (nf < 2 || nf > 12288 || !(df > 0) || !std::isfinite(df) || !M || !xs || nrec < 1 || nrec > (1 << 20) || !rec ||
+        nt < 1 || !(dt > 0) || !(fp > 0) || !std::isfinite(t0) || !traces || wave < 1 || wave > 256)
+        return fail(base, LSM_ERR_ARG,
+                    "lsm_seismograms: need 2 <= nf <= 12288, df, dt, fp > 0, 1 <= nrec, nt >= 1, 1 <= wave <= 256 and "
+                    "non-null pointers");
+    Store* s = base->s;
+    const Dims& d = s->d;
+    std::vector<long long> node(nrec);
+    for (int r = 0; r < nrec; ++r) {
+        const int ix = rec[3 * r], iy = rec[3 * r + 1], iz = rec[3 * r + 2];
+        if (ix < 0 || ix >= d.nx || iy < 0 || iy >= d.ny || iz < 0 || iz >= d.nz)
+            return fail(base, LSM_ERR_ARG, "lsm_seismograms: receiver node outside the grid");
+        node[r] = ((long long)iz * d.ny + iy) * d.nx + ix;
+    }
+    const cudaStream_t st = s->st;
+    const long long ntr = 3LL * nrec;
+    long long* d_node = nullptr;
+    double2* d_U = nullptr;
+    CK(base, cudaMalloc(&d_node, nrec * sizeof(long long)));
+    cudaError_t e = cudaMalloc(&d_U, (size_t)nf * ntr * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_node, node.data(), nrec * sizeof(long long), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_U, 0, (size_t)nf * ntr * sizeof(double2), st);
+    lsm_status rc = e == cudaSuccess ? LSM_OK : cuda_fail(base, e, "lsm_seismograms: receiver buffers");
+    bool on_node = false;
+    if (iters) iters[0] = 0;
+    if (relres) relres[0] = 0.0;
+    const size_t fbytes = 3 * (size_t)d.N * sizeof(double2);
+    for (int k0 = 1; k0 < nf && rc == LSM_OK; k0 += wave) {
+        const int m = (nf - k0 < wave) ? nf - k0 : wave;
+        std::vector<lsm_t> hs(m, nullptr);
+        std::vector<void*> bs(m, nullptr), xv(m, nullptr);
+        std::vector<int> it(m, 0);
+        std::vector<double> rr(m, 0.0);
+        for (int j = 0; j < m && rc == LSM_OK; ++j) {
+            rc = lsm_create_shared(&hs[j], base, 2.0 * M_PI * (k0 + j) * df);
+            if (rc != LSM_OK) {
+                base->err = std::string("lsm_seismograms: ") + g_err;
+                break;
+            }
+            e = cudaMalloc(&bs[j], fbytes);
+            if (e == cudaSuccess) e = cudaMalloc(&xv[j], fbytes);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(base, e, "lsm_seismograms: fields");
+                break;
+            }
+            const lsm_status r0 = lsm_source(hs[j], M, xs, bs[j]);
+            if (r0 == LSM_WARN_SOURCE_ON_NODE) on_node = true;
+            else if (r0 != LSM_OK) {
+                base->err = hs[j]->err;
+                rc = r0;
+                break;
+            }
+            e = cudaMemsetAsync(xv[j], 0, fbytes, st);
+            if (e != cudaSuccess) rc = cuda_fail(base, e, "lsm_seismograms: initial guess");
+        }
+        if (rc == LSM_OK) {
+            rc = lsm_solve_batched(m, hs.data(), bs.data(), xv.data(), it.data(), rr.data(), nullptr);
+            if (rc != LSM_OK) base->err = "lsm_seismograms: " + hs[0]->err;
+        }
+        for (int j = 0; j < m && rc == LSM_OK; ++j) {
+            e = launch_gather_receivers((const double2*)xv[j], d.N, d_node, nrec, d_U + (size_t)(k0 + j) * ntr, st);
+            if (e != cudaSuccess) rc = cuda_fail(base, e, "lsm_seismograms: receiver gather");
+            base->nl += 1;
+            if (iters) iters[k0 + j] = it[j];
+            if (relres) relres[k0 + j] = rr[j];
+        }
+        cudaStreamSynchronize(st);
+        for (int j = 0; j < m; ++j) {
+            cudaFree(bs[j]);
+            cudaFree(xv[j]);
+            if (hs[j]) {
+                base->nl += hs[j]->nl;
+                lsm_destroy(hs[j]);
+            }
+        }
+    }
+    if (rc == LSM_OK) {
+        e = launch_time_traces(nf, df, (int)ntr, d_U, nt, dt, fp, t0, traces, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(base, e, "lsm_seismograms: time traces");
+        base->nl += 1;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(d_node);
+    cudaFree(d_U);
+    if (rc == LSM_OK && on_node) {
+        base->err = "lsm_seismograms: a grid node coincides with the source; u0 set to 0 there";
+        return LSM_WARN_SOURCE_ON_NODE;
+    }
+    return rc;
 }

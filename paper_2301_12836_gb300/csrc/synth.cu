@@ -50,4 +50,21 @@ cudaError_t launch_time_traces(int nf, double df, int ntr, const double2* U, int
     return cudaGetLastError();
 }
 
+// Receiver gather: out[r * 3 + c] = u[c * N + node[r]] for nrec receivers (node = linear index
+// (iz ny + iy) nx + ix), one row of the [nf][3 nrec] spectra array of the seismogram chain.
+__global__ void k_gather_receivers(const double2* __restrict__ u, long long N, const long long* __restrict__ node, int nrec,
+                                   double2* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * nrec) return;
+    const int r = i / 3, c = i - 3 * r;
+    out[i] = u[(long long)c * N + node[r]];
+}
+
+cudaError_t launch_gather_receivers(const double2* u, long long N, const long long* node, int nrec, double2* out,
+                                    cudaStream_t st) {
+    const int n = 3 * nrec;
+    k_gather_receivers<<<(n + 255) / 256, 256, 0, st>>>(u, N, node, nrec, out);
+    return cudaGetLastError();
+}
+
 }  // namespace lsm

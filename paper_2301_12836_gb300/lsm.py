@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "LSM_OK", -1: "LSM_ERR_ARG", -2: "LSM_ERR_CUDA", -3: "LSM_ERR
 # every symbol the header declares, in declaration order
 EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", "lsm_source_moments", "lsm_apply", "lsm_apply_c64",
            "lsm_apply_df", "lsm_adjoint", "lsm_solve", "lsm_solve_batched", "lsm_solve_adjoint", "lsm_set_contrast", "lsm_gradient",
-           "lsm_source_gradient", "lsm_time_traces", "lsm_set_schedule", "lsm_get_schedule", "lsm_autotune", "lsm_dot_c64", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
+           "lsm_source_gradient", "lsm_time_traces", "lsm_seismograms", "lsm_set_schedule", "lsm_get_schedule", "lsm_autotune", "lsm_dot_c64", "lsm_launch_count", "lsm_timer_start", "lsm_timer_read",
            "lsm_apply_static", "lsm_destroy", "lsm_last_error")
 
 
@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
     lib.lsm_source_gradient.restype = i
     lib.lsm_time_traces.argtypes = [i, d, i, vp, i, d, d, d, vp, vp]
     lib.lsm_time_traces.restype = i
+    lib.lsm_seismograms.argtypes = [vp, i, d, ct.POINTER(d), ct.POINTER(d), i, ct.POINTER(i), i, d, d, d, vp, i,
+                                     ct.POINTER(i), ct.POINTER(d)]
+    lib.lsm_seismograms.restype = i
     lib.lsm_launch_count.argtypes = [vp]
     lib.lsm_launch_count.restype = ct.c_longlong
     lib.lsm_timer_start.argtypes = [vp, i]
@@ -283,6 +286,23 @@ def lsm_time_traces(spectra: torch.Tensor, df, nt, dt, fp, t0, stream: torch.cud
     _check(load().lsm_time_traces(int(nf), float(df), int(ntr), _ptr(spectra, torch.complex128, nf * ntr), int(nt),
                                   float(dt), float(fp), float(t0), _ptr(out, torch.float64, ntr * nt), ct.c_void_p(st)))
     return out
+
+
+def lsm_seismograms(base: Handle, nf, df, M6, xs, receivers, nt, dt, fp, t0, wave=32):
+    """Receiver traces of one source over f_k = k df (k < nf): returns (status, traces (nrec, 3, nt)
+    device float64, iterations [nf], relres [nf]).  receivers: (nrec, 3) node indices (ix, iy, iz)."""
+    rec = [int(v) for r in receivers for v in r]
+    nrec = len(rec) // 3
+    out = torch.empty((nrec, 3, int(nt)), dtype=torch.float64, device=base.device)
+    M = (ct.c_double * 6)(*[float(v) for v in M6])
+    x = (ct.c_double * 3)(*[float(v) for v in xs])
+    R = (ct.c_int * len(rec))(*rec)
+    it = (ct.c_int * int(nf))()
+    rr = (ct.c_double * int(nf))()
+    code = load().lsm_seismograms(base.ptr, int(nf), float(df), M, x, nrec, R, int(nt), float(dt), float(fp), float(t0),
+                                  _ptr(out, torch.float64, nrec * 3 * int(nt)), int(wave), it, rr)
+    _check(code, base.ptr, allow=(LSM_WARN_SOURCE_ON_NODE,))
+    return code, out, list(it), list(rr)
 
 
 def lsm_launch_count(h: Handle) -> int:

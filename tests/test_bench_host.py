@@ -13,6 +13,22 @@ def test_stage_bytes_model_128():
     assert mb == [327, 369, 308, 509, 302, 201]
     # complex128 / double-float pairs move exactly twice the bytes
     assert all(bench.stage_bytes(s, N128, 16, 8) == 2 * bench.stage_bytes(s, N128, 8, 4) for s in range(6))
+    # the z pass stages each frequency's octant spectrum (6 x 129^3 complex) once for the systems of
+    # a launch that share it: with 8 sources per frequency its bytes per system apply fall to 419 MB
+    g = 6 * 129 ** 3 * 8
+    assert bench.stage_bytes(3, N128, 8, 4, share=8) == bench.stage_bytes(3, N128, 8, 4) - g * 7 / 8
+    assert round(bench.stage_bytes(3, N128, 8, 4, share=8) / 1e6) == 419
+    assert all(bench.stage_bytes(s, N128, 8, 4, share=8) == bench.stage_bytes(s, N128, 8, 4) for s in (0, 1, 2, 4, 5))
+
+
+def test_waves_cover_every_frequency():
+    blocks = bench.freq_blocks(32, 8)
+    assert blocks == [list(range(8 * k, 8 * k + 8)) for k in range(4)]
+    assert bench.freq_blocks(10, 4) == [[0, 1, 2, 3], [4, 5, 6, 7], [8, 9]]
+    # timed steps start at the first wave and cycle: 4 steps cover each of the 32 frequencies once
+    seq = bench.rank_blocks(0, 1, 4, 4)
+    assert sorted(f for b in seq for f in blocks[b]) == list(range(32))
+    assert bench.rank_blocks(0, 1, 20, 4) == [0, 1, 2, 3] * 5
 
 
 def _pinned_digest():
@@ -21,6 +37,13 @@ def _pinned_digest():
             if line.startswith("csrc_sha256:"):
                 return line.split(":", 1)[1].strip()
     return None
+
+
+def test_traffic_records_parse():
+    recs = bench.traffic_records()
+    assert recs, "profiles/roofline_traffic.txt holds at least one record"
+    for r in recs:
+        assert {"stage", "precision", "grid_voxels", "dram_bytes_per_system_apply", "csrc_sha256"} <= set(r)
 
 
 def test_traffic_pin_lookup():

@@ -1,7 +1,7 @@
 """The multi-rank (replicas) path of bench.py on CPU with the gloo backend, world size 2.
 
-Each (frequency, source) system is independent, so ranks take disjoint frequencies and exchange
-only the timing: the slowest rank's time and the sums of the work counters.
+Each (frequency, source) system is independent, so every rank solves its own waves of frequencies
+and ranks exchange only the timing: the slowest rank's time and the sums of the work counters.
 """
 import os
 import socket
@@ -22,7 +22,7 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    f = bench.rank_frequencies(rank, world, 8, 32)
+    f = bench.rank_blocks(rank, world, 8, 4)
     ms = 100.0 + 50.0 * rank                 # rank 1 is the slow one
     out = bench.reduce_timing(ms, applies=10 * (rank + 1), solves=8, launches=70, world=world, dist=dist)
     q.put((rank, f, out))
@@ -43,7 +43,10 @@ def test_two_ranks_shard_frequencies_and_reduce_timing():
         assert p.exitcode == 0
     f0, o0 = res[0]
     f1, o1 = res[1]
-    assert set(f0).isdisjoint(f1) and len(set(f0)) == 8 and len(set(f1)) == 8
+    # replicas: each rank cycles through all four waves (the same mix of work), and at every step
+    # the two ranks solve different waves
+    assert sorted(f0) == sorted(f1) == [0, 0, 1, 1, 2, 2, 3, 3]
+    assert all(a != b for a, b in zip(f0, f1))
     # both ranks see the same whole-job numbers: max time, summed work
     assert o0 == o1 == (150.0, 30.0, 16.0, 140.0)
 
@@ -51,6 +54,7 @@ def test_two_ranks_shard_frequencies_and_reduce_timing():
 def test_single_rank_passthrough():
     import bench
     assert bench.rank_frequencies(0, 1, 5, 32) == [0, 1, 2, 3, 4]
+    assert bench.rank_frequencies(0, 1, 2, 32, per_wave=8) == list(range(16))
     assert bench.reduce_timing(12.5, 3, 2, 9, world=1) == (12.5, 3.0, 2.0, 9.0)
 
 
