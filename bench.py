@@ -57,6 +57,8 @@ def parse(argv=None):
     ap.add_argument("--systems", type=int, default=8, help="moment tensors per frequency")
     ap.add_argument("--wave-freqs", type=int, default=8, help="frequencies per memory wave (one batched solve)")
     ap.add_argument("--inner-tol", type=float, default=None, help="floor of the FP32 inner tolerance (mixed)")
+    ap.add_argument("--maxit", type=int, default=2000, help="BiCGSTAB iteration limit (per inner solve when mixed)")
+    ap.add_argument("--max-outer", type=int, default=None, help="mixed: refinement steps limit")
     ap.add_argument("--kernel", default="diff", choices=["diff", "h"],
                     help="operator form: difference form (default) or sampled analytic H (Eq. 21 literally)")
     ap.add_argument("--residual", default="fp64", choices=["fp64", "df"],
@@ -490,6 +492,11 @@ def stage_records(lsm, st_ms, st_launch, a64, a32, ms, n, kernel, pair, share):
                         "model_flops_per_system_apply": fl,
                         "hbm_gbs": round(nbytes * napp / (st_ms[slot] / 1e3) / 1e9, 1),
                         "algorithmic_bytes_per_system_apply": round(nbytes)})
+        if kernel == "diff":
+            t = traffic_from_profile(stage, "mixed" if f32 else ("dfloat" if pair else "fp64"), n, share)
+            if t is not None:
+                rec["traffic"] = round(t)
+                rec["traffic_over_algorithmic"] = round(t / rec["algorithmic_bytes_per_system_apply"], 3)
         stages.append(rec)
     stages.sort(key=lambda r: -r["ms"])
     return stages
@@ -522,10 +529,12 @@ def main():
     kern = lsm.LSM_KERNEL_H if args.kernel == "h" else lsm.LSM_KERNEL_DIFF
 
     def mk_opts(precision, residual):
-        o = lsm.lsm_default_opts(precision=precision, tol=wl.tol, maxit=2000, kernel=kern,
+        o = lsm.lsm_default_opts(precision=precision, tol=wl.tol, maxit=args.maxit, kernel=kern,
                                  residual=lsm.LSM_RESIDUAL_DFLOAT if residual == "df" else lsm.LSM_RESIDUAL_FP64)
         if args.inner_tol:
             o.inner_tol = args.inner_tol
+        if args.max_outer:
+            o.max_outer = args.max_outer
         return o
 
     t_setup = time.perf_counter()

@@ -28,13 +28,13 @@ class ReceiverModel:
     """
 
     def __init__(self, n, dx, lam0, mu0, rho0, dC0, drho0, freqs_hz, xs, receivers, precision=lsm.LSM_FP64,
-                 tol=1e-10, maxit=2000, checkpoint=False):
+                 tol=1e-10, maxit=2000, checkpoint=False, max_outer=8):
         import numpy as np
         self.n = tuple(int(v) for v in n)
         nx, ny, nz = self.n
         self.N = nx * ny * nz
         self.xs = [float(v) for v in xs]
-        opts = lsm.lsm_default_opts(precision=precision, tol=tol, maxit=maxit)
+        opts = lsm.lsm_default_opts(precision=precision, tol=tol, maxit=maxit, max_outer=max_outer)
         ws = [2.0 * np.pi * float(f) for f in freqs_hz]
         self.base = lsm.lsm_create(self.n, dx, lam0, mu0, rho0, dC0, drho0, ws[0], opts)
         self.handles = [self.base] + [lsm.lsm_create_shared(self.base, w) for w in ws[1:]]

@@ -466,104 +466,89 @@ __global__ void __launch_bounds__(3 * TX * FourStep<A LSM_COMMA B>::TPL, 2) k4_f
     }
 }
 
-// Register-resident FP32 z pass for L = A * A.  Thread (lx, q) of a TX x A block owns column
-// x0 + lx and, for each of the three components, the step-1 DFT of t = q and the step-2 DFT of
-// k1 = q.  The forward step 2 leaves X[q + A k2] (k2 = 0..A-1) of all three components in its
-// registers: exactly the inputs the inverse transform's step 1 needs for t = q, and all three
-// components of the same frequencies, so the Green multiply runs in registers and each transform
-// crosses shared memory once.  A block serves its (kx tile, ky) column for every system of the
-// batch: the next system's input rows (only the nin rows that can be nonzero) are copied into
-// shared memory asynchronously while the current one is transformed, and the spectrum slice is
-// staged once per frequency, as in k4_fftz_green.
+// Register-resident FP32 z pass for L = A * A, two y rows per block.  Block (x tile, j) serves the
+// columns x0 .. x0 + TX - 1 of the rows ky = j and Ly - j (j = 0 and j = ny, their own mirror
+// images, are served alone: the second half of the block repeats the first row's arithmetic and
+// stores nothing).  Both rows read the same octant slice of the spectrum (fy = j; the odd entries
+// flip sign in the mirrored row), so the slice is staged once for both and a warp's spectrum loads
+// for the two rows are one shared-memory access.  Thread (lx, r, q) owns column x0 + lx of row r
+// and, for each of the three components, the step-1 DFT of t = q and the step-2 DFT of k1 = q:
+// the forward step 2 leaves X[q + A k2] (k2 = 0..A-1) of all three components in its registers,
+// exactly the inputs of the inverse transform's step 1 for t = q, so the Green multiply runs in
+// registers and each transform crosses shared memory once.  The nonzero inputs are loaded straight
+// from global memory.  A block serves its columns for every system of the batch, restaging the
+// spectrum slice only when the frequency changes.
 template <bool CONJ, int A, int TX>
-__global__ void __launch_bounds__(TX * A, 4) k4z_reg(
+__global__ void __launch_bounds__(2 * TX * A, 3) k4z_pair(
     Dims d, const float2* __restrict__ tw, const ApplySys<float>* __restrict__ sys, int nsys, int in_count, int in_off,
     int out_count, int out_off, int src_sel, int dst_sel) {
     typedef float2 C;
-    constexpr int L = A * A, NT = TX * A;
+    constexpr int L = A * A, NL = 2 * TX, NT = NL * A, NZ = A / 2 + 1;
     constexpr int E = 16;                                            // float2 per 128-byte bank row
-    constexpr int YS = A * TX + (((TX - A * TX) % E) + E) % E;       // row stride of Y[t][.]
-    const int nin = in_off + in_count;    // rows of a padded line that can be nonzero (<= L)
+    constexpr int YS = A * NL + (((NL - A * NL) % E) + E) % E;       // row stride of Y[t][.]
+    const int nin = in_off + in_count;    // rows of a padded line that can be nonzero (<= NZ A)
     extern __shared__ unsigned char smem_raw[];
     C* sY = reinterpret_cast<C*>(smem_raw);   // two exchange buffers of A * YS, used alternately
-    C* sX = sY + 2 * A * YS;              // [3][nin][TX] inputs of the system in flight
-    C* sG = sX + 3 * nin * TX;            // [6][nz+1][TX] spectrum slice: a warp's reads are contiguous
+    C* sG = sY + 2 * A * YS;              // [6][nz+1][TX] spectrum slice
     C* sW = sG + 6 * (d.nz + 1) * TX;     // twiddles exp(-2 pi i k / L), k < L
     const int lx = threadIdx.x % TX;
-    const int q0 = threadIdx.x / TX;
-    const int ky = blockIdx.y;
+    const int r = (threadIdx.x / TX) & 1;
+    const int q0 = threadIdx.x / NL;
+    const int l = lx + TX * r;            // line of the exchange buffers
+    const int j = blockIdx.y;             // 0 .. ny
+    const bool alone = j == 0 || j == d.ny;
+    const int ky = (r == 0 || alone) ? j : d.Ly - j;
+    const bool owner = r == 0 || !alone;
     const int x0 = blockIdx.x * TX;
     const int kx = x0 + lx;
     const bool xin = kx < d.Lx;
-    const int fy = ky <= d.ny ? ky : d.Ly - ky;
     const unsigned my = ky > d.ny ? SIGN_BIT : 0u;
     const unsigned mx = kx > d.nx ? SIGN_BIT : 0u;
     const long long NO = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const int GC = (d.nz + 1) * TX;
-    const int plane = d.Ly * d.Lx;        // < 2^18, so element offsets below fit in 32 bits
-    auto running = [&](int j) { return !sys[j].run || *sys[j].run; };
-    auto next_running = [&](int j) {
-        while (j < nsys && !running(j)) ++j;
-        return j;
-    };
-    // copy the nin input rows of system j's column tile into sX (rows before in_off are zero)
-    auto prefetch = [&](int j) {
-        const ApplySys<float> P = sys[j];
-        const C* base = pick<C>(P, src_sel) + (long long)ky * d.Lx + x0;
-        for (int i = threadIdx.x; i < 3 * nin * TX; i += NT) {
-            const int l = i % TX;
-            const int r = i / TX;
-            const int e = r % nin;
-            const int c = r / nin;
-            const int es = e - in_off;
-            C* to = &sX[(c * nin + e) * TX + l];
-            if (x0 + l < d.Lx && es >= 0) cp_async_elem(to, base + (long long)c * in_count * plane + (long long)es * plane + l);
-            else *to = czero<C>();
-        }
-        cp_async_commit();
-    };
-    for (int i = threadIdx.x; i < L; i += NT) sW[i] = tw[i];   // ordered before use by the loop's first barrier
-    int si = next_running(0);
-    if (si < nsys) prefetch(si);
+    const int plane = d.Ly * d.Lx;
+    const long long colofs = (long long)ky * d.Lx + kx;
+    for (int i = threadIdx.x; i < L; i += NT) sW[i] = tw[i];   // ordered before use by the first barrier
     const C* staged = nullptr;
-    while (si < nsys) {
+    for (int si = 0; si < nsys; ++si) {
         // q re-read through an opaque move: everything derived from it (rows, offsets, masks,
         // twiddle indices) is recomputed per system instead of held in registers across systems
         int q;
         asm volatile("mov.u32 %0, %1;" : "=r"(q) : "r"(q0));
         const ApplySys<float> S = sys[si];
-        const int sn = next_running(si + 1);
-        cp_async_wait_all();
-        __syncthreads();   // sX holds this system's rows; the previous system is done with sG and sY
+        if (S.run && !*S.run) continue;
         const bool fresh = S.ghat != staged;
         if (fresh) {
-            for (int i = threadIdx.x; i < (d.nz + 1) * 6 * TX; i += NT) {
-                const int l = i % TX;
-                const int r = i / TX;
-                const int c = r % 6;
-                const int fz = r / 6;
-                const int kxx = x0 + l;
-                if (kxx < d.Lx) {
-                    const int fx = kxx <= d.nx ? kxx : d.Lx - kxx;
-                    cp_async_elem(&sG[c * GC + fz * TX + l], S.ghat + c * NO + ((long long)fz * (d.ny + 1) + fy) * (d.nx + 1) + fx);
-                }
+            __syncthreads();   // the previous slice's last reads (and the twiddle fill) are done
+            // slice element i = (c (nz+1) + fz) TX + lxx; this thread copies i = tid + k NT
+            const int lxx = threadIdx.x % TX;
+            const int kxx = x0 + lxx;
+            const int fx = kxx <= d.nx ? kxx : d.Lx - kxx;
+            int row = threadIdx.x / TX;
+            for (int i = threadIdx.x; i < 6 * GC; i += NT, row += NT / TX) {
+                const int c = row / (d.nz + 1);
+                const int fz = row - c * (d.nz + 1);
+                if (kxx < d.Lx)
+                    cp_async_elem(&sG[i], S.ghat + c * NO + ((long long)fz * (d.ny + 1) + j) * (d.nx + 1) + fx);
             }
             cp_async_commit();
             staged = S.ghat;
         }
+        const C* __restrict__ src = pick<C>(S, src_sel) + colofs;
         C R[3][A];
-        // ---- forward transforms, one component at a time through sY
+        // ---- forward transforms, one component at a time through the exchange buffers
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             C v[A];
-            const C* xc = sX + c * nin * TX + lx;
+            const C* xc = src + (long long)c * in_count * plane;
             // at most A/2 + 1 nonzero inputs per step-1 DFT (nin <= (A/2 + 1) A, checked at launch)
 #pragma unroll
             for (int a = 0; a < A; ++a) {
                 const int e = q + A * a;
-                v[a] = (a < A / 2 + 1 && e < nin) ? xc[e * TX] : czero<C>();
+                const int es = e - in_off;
+                v[a] = (a < NZ && e < nin && es >= 0 && xin) ? xc[(long long)es * plane] : czero<C>();
             }
-            dft_reg_p<A, -1, A / 2 + 1, A>(v);
+            dft_reg_p<A, -1, NZ, A>(v);
             if (q) {
 #pragma unroll
                 for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], lds_fresh(&sW[q * k1]));
@@ -571,17 +556,14 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
             // buffer c & 1 was last read two components ago, before the previous barrier
             C* Y = sY + (c & 1) * A * YS;
 #pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) Y[q * YS + k1 * TX + lx] = v[k1];
+            for (int k1 = 0; k1 < A; ++k1) Y[q * YS + k1 * NL + l] = v[k1];
             __syncthreads();
-            if (c == 2 && sn < nsys) prefetch(sn);   // every read of sX is done
 #pragma unroll
-            for (int t = 0; t < A; ++t) R[c][t] = Y[t * YS + q * TX + lx];
+            for (int t = 0; t < A; ++t) R[c][t] = Y[t * YS + q * NL + l];
             dft_reg<A, -1>(R[c]);   // R[c][k2] = X_c[q + A k2]
         }
         if (fresh) {
-            // the slice's group is complete; the prefetch committed after it may still be in flight
-            if (sn < nsys) cp_async_wait_group<1>();
-            else cp_async_wait_all();
+            cp_async_wait_all();
             __syncthreads();
         }
         // ---- Green multiply in registers
@@ -596,14 +578,14 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
                 const C G3 = flip_sign(g[3 * GC], my ^ mz);
                 const C G4 = flip_sign(g[4 * GC], mx ^ mz);
                 const C G5 = flip_sign(g[5 * GC], mx ^ my);
-                const C q0 = R[0][k2], q1 = R[1][k2], q2 = R[2][k2];
-                R[0][k2] = gdot3<CONJ>(G0, q0, G5, q1, G4, q2);
-                R[1][k2] = gdot3<CONJ>(G5, q0, G1, q1, G3, q2);
-                R[2][k2] = gdot3<CONJ>(G4, q0, G3, q1, G2, q2);
+                const C qa = R[0][k2], qb = R[1][k2], qc = R[2][k2];
+                R[0][k2] = gdot3<CONJ>(G0, qa, G5, qb, G4, qc);
+                R[1][k2] = gdot3<CONJ>(G5, qa, G1, qb, G3, qc);
+                R[2][k2] = gdot3<CONJ>(G4, qa, G3, qb, G2, qc);
             }
         }
         // ---- inverse transforms: step 1 of t = q takes R[c][a] as its input a
-        C* __restrict__ dst = pick<C>(S, dst_sel) + ky * d.Lx + kx;
+        C* __restrict__ dst = pick<C>(S, dst_sel) + colofs;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             dft_reg<A, 1>(R[c]);
@@ -615,20 +597,19 @@ __global__ void __launch_bounds__(TX * A, 4) k4z_reg(
             // barrier of the component before
             C* Y = sY + ((c + 1) & 1) * A * YS;
 #pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) Y[q * YS + k1 * TX + lx] = R[c][k1];
+            for (int k1 = 0; k1 < A; ++k1) Y[q * YS + k1 * NL + l] = R[c][k1];
             __syncthreads();
             C v[A];
 #pragma unroll
-            for (int t = 0; t < A; ++t) v[t] = Y[t * YS + q * TX + lx];
-            dft_reg_p<A, 1, A, A / 2 + 1>(v);   // outputs k < (A/2 + 1) A only (checked at launch)
+            for (int t = 0; t < A; ++t) v[t] = Y[t * YS + q * NL + l];
+            dft_reg_p<A, 1, A, NZ>(v);   // outputs k < (A/2 + 1) A only (checked at launch)
             C* dc = dst + (long long)c * out_count * plane;
 #pragma unroll
-            for (int k2 = 0; k2 < A / 2 + 1; ++k2) {
+            for (int k2 = 0; k2 < NZ; ++k2) {
                 const int eo = q + A * k2 - out_off;
-                if (xin && eo >= 0 && eo < out_count) dc[eo * plane] = v[k2];
+                if (owner && xin && eo >= 0 && eo < out_count) dc[(long long)eo * plane] = v[k2];
             }
         }
-        si = sn;
     }
 }
 
@@ -1432,13 +1413,12 @@ static void launch_zpass(const Dims& d, const ApplySys<T>* sys, int nsys, const 
         }
         if constexpr (F::INPLACE && sizeof(T) == 4 && F::A_ == F::B_) {
           if (v != 3) {
-            constexpr int A = F::A_, TXR = 4;
+            constexpr int A = F::A_, TXR = 4, NL = 2 * TXR;
             constexpr int E = 16;
-            constexpr int YS = A * TXR + (((TXR - A * TXR) % E) + E) % E;
-            const size_t smr = ((size_t)2 * A * YS + (size_t)3 * (in_off + in_count) * TXR + (size_t)6 * (d.nz + 1) * TXR +
-                                (size_t)A * A) * sizeof(C);
-            smem_attr((const void*)k4z_reg<CONJ, A, TXR>, smr);
-            k4z_reg<CONJ, A, TXR><<<dim3(cdiv(d.Lx, TXR), d.Ly, 1), TXR * A, smr, st>>>(
+            constexpr int YS = A * NL + (((NL - A * NL) % E) + E) % E;
+            const size_t smr = ((size_t)2 * A * YS + (size_t)6 * (d.nz + 1) * TXR + (size_t)A * A) * sizeof(C);
+            smem_attr((const void*)k4z_pair<CONJ, A, TXR>, smr);
+            k4z_pair<CONJ, A, TXR><<<dim3(cdiv(d.Lx, TXR), d.ny + 1, 1), 2 * TXR * A, smr, st>>>(
                 d, (const float2*)pl.twz, (const ApplySys<float>*)sys, nsys, in_count, in_off, out_count, out_off,
                 src_sel, dst_sel);
             return;

@@ -912,13 +912,14 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             rc = run_bicgstab<float>(h0, hs, nsys, itol, h0->o.maxit, true, w.ms, fin, adjoint);
             if (rc != LSM_OK) return rc;
             for (int i = 0; i < nsys; ++i) it_out[i] += fin[i].iters;
-            CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
+            CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, w.st, n3, nsys, nblk, st,
+                          &h0->nl));
         }
         CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
         CK(h0, cudaStreamSynchronize(st));
         for (int i = 0; i < nsys; ++i) {
             rr_out[i] = ms[i].relres;
-            stat[i] = ms[i].done ? LSM_OK : LSM_ERR_NOCONV;
+            stat[i] = (ms[i].done && !ms[i].stalled) ? LSM_OK : LSM_ERR_NOCONV;
             if (ms[i].bnorm2 == 0.0) CK(h0, cudaMemsetAsync(x[i], 0, n3 * sizeof(double2), st));
         }
         CK(h0, cudaStreamSynchronize(st));

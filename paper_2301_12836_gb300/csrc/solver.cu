@@ -496,10 +496,13 @@ __global__ void __launch_bounds__(VTH) k_mix_to_pair(const double2* const* __res
              });
 }
 
+// the inner solve ended with a finite residual below the norm of its right-hand side
+__device__ __forceinline__ bool inner_progress(const BcgState& I) { return isfinite(I.rnorm2) && I.rnorm2 < I.bnorm2; }
+
 __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64, float2* const* __restrict__ d32,
-                                                MixState* __restrict__ ms, long long n) {
+                                                MixState* __restrict__ ms, const BcgState* __restrict__ inner, long long n) {
     const int sys = blockIdx.y;
-    if (ms[sys].done) return;
+    if (ms[sys].done || !inner_progress(inner[sys])) return;
     const double sc = sqrt(ms[sys].rnorm2);
     double2* X = x64[sys];
     const float2* D = d32[sys];
@@ -512,6 +515,16 @@ __global__ void __launch_bounds__(VTH) k_mix_up(double2* const* __restrict__ x64
                  x.y += sc * (double)w.d.y;
                  X[i] = x;
              });
+}
+
+// after k_mix_up: a system whose inner solve made no progress stops refining (its next inner solve
+// would repeat this one exactly); the host reports it as not converged
+__global__ void k_mix_stall(MixState* __restrict__ ms, const BcgState* __restrict__ inner, int nsys) {
+    const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sys >= nsys || ms[sys].done || inner_progress(inner[sys])) return;
+    ms[sys].done = 1;
+    ms[sys].stalled = 1;
+    ms[sys].run = 0;
 }
 
 // conj(a) . b of complex64 vectors with the inner-product accumulation of the FP32 solver kernels:
@@ -628,10 +641,11 @@ cudaError_t mix_to_pair(const double2* const* x64, dfcplx* const* xdf, MixState*
     if (nl) *nl += 1;
     return cudaGetLastError();
 }
-cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, long long n, int nsys, int nblk, cudaStream_t s,
-                   long long* nl) {
-    k_mix_up<<<dim3(nblk, nsys), VTH, 0, s>>>(x64, d32, ms, n);
-    if (nl) *nl += 1;
+cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, const BcgState* inner, long long n, int nsys, int nblk,
+                   cudaStream_t s, long long* nl) {
+    k_mix_up<<<dim3(nblk, nsys), VTH, 0, s>>>(x64, d32, ms, inner, n);
+    k_mix_stall<<<(nsys + 127) / 128, 128, 0, s>>>(ms, inner, nsys);
+    if (nl) *nl += 2;
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ struct MixState {
     double xnorm2;      // ||x||^2 of the initial iterate
     int pexp;           // double-float residual apply: x entered scaled by 2^-pexp
     int rpair;          // the residual buffer holds double-float pairs scaled by 2^-pexp
+    int stalled;        // an inner solve ended without reducing its residual: refinement stopped
 };
 
 struct Partials {
@@ -86,7 +87,9 @@ cudaError_t mix_to_pair(const double2* const* x64, dfcplx* const* xdf, MixState*
                         cudaStream_t s, long long* nl);
 cudaError_t mix_down(double2* const* r64, float2* const* r32, const MixState* ms, long long n, int nsys, int nblk,
                      cudaStream_t s, long long* nl);
-cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, long long n, int nsys, int nblk,
+// x += ||r|| d for the systems whose inner solve (state inner[sys]) reduced its residual; a system
+// whose inner solve did not (or ended non-finite) keeps x and is marked done and stalled.
+cudaError_t mix_up(double2* const* x64, float2* const* d32, MixState* ms, const BcgState* inner, long long n, int nsys, int nblk,
                    cudaStream_t s, long long* nl);
 
 int vec_blocks(long long n);

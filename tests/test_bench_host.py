@@ -47,15 +47,18 @@ def test_traffic_records_parse():
 
 
 def test_traffic_pin_lookup():
-    t = bench.traffic_from_profile(3, "mixed", N128)
+    t = bench.traffic_from_profile(3, "mixed", N128, 8)
     if _pinned_digest() != bench._csrc_digest():
         # the kernels changed since the capture: the bench must not report stale counters
         assert t is None
         return
-    # the FP32 z pass reads and writes a little less than its algorithmic bytes (the spectrum is
-    # shared by the two systems of the capture): no wasted re-reads
-    assert t is not None and 0.9 < t / bench.stage_bytes(3, N128, 8, 4) < 1.0
-    assert bench.traffic_from_profile(3, "fp64", N128) is None
-    assert bench.traffic_from_profile(2, "mixed", N128) is None
+    # every stage of both precisions is pinned, each within 15% of its algorithmic bytes (no
+    # wasted re-reads); the z pass shares the spectrum among the 8 systems of a frequency
+    for st in range(6):
+        for prec, b, c in (("mixed", 8, 4), ("fp64", 16, 8)):
+            v = bench.traffic_from_profile(st, prec, N128, 8)
+            assert v is not None and 0.85 < v / bench.stage_bytes(st, N128, b, c, 8) < 1.15, (st, prec)
+    assert bench.traffic_from_profile(3, "dfloat", N128, 8) is None
+    assert bench.traffic_from_profile(3, "mixed", N128, 2) is None      # another sharing: not pinned
     # scaled to another grid by the number of voxels
-    assert abs(bench.traffic_from_profile(3, "mixed", (64, 64, 64)) - t / 8) < 1.0
+    assert abs(bench.traffic_from_profile(3, "mixed", (64, 64, 64), 8) - t / 8) < 1.0
