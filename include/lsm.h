@@ -93,11 +93,12 @@ typedef struct {
                           adjoint calls (lsm_adjoint, lsm_solve_adjoint, lsm_gradient) and
                           lsm_apply_static return LSM_ERR_ARG for it. */
     int residual;      /* LSM_MIXED: arithmetic of the outer residual's operator apply.
-                          LSM_RESIDUAL_DFLOAT (default): double-float pairs (two FP32 words,
-                          about 48 significand bits, unit roundoff near 2^-48; see
-                          lsm_apply_df) on the FP32 pipe, with the iterate scaled by a power
-                          of two to RMS(b) ~ 1 first; LSM_RESIDUAL_FP64: FP64.  Adjoint
-                          solves always use FP64.  Ignored for LSM_FP64 handles. */
+                          LSM_RESIDUAL_FP64 (default): FP64.  LSM_RESIDUAL_DFLOAT: double-float
+                          pairs (two FP32 words, about 48 significand bits, unit roundoff near
+                          2^-48; see lsm_apply_df) on the FP32 pipe, with the iterate scaled by a
+                          power of two to RMS(b) ~ 1 first: several times faster on this GPU,
+                          whose FP64 rate is 1/64 of its FP32 rate, but narrower than FP64.
+                          Adjoint solves always use FP64.  Ignored for LSM_FP64 handles. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */

@@ -235,7 +235,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->taper = 0;
     o->graph = 1;
     o->kernel = LSM_KERNEL_DIFF;
-    o->residual = LSM_RESIDUAL_DFLOAT;
+    o->residual = LSM_RESIDUAL_FP64;
 }
 
 static lsm_status build_spectrum(lsm_t h) {

@@ -49,6 +49,7 @@ def test_default_opts(lib):
     assert o.precision == lsm.LSM_FP64 and o.green == lsm.LSM_GREEN_EXACT
     assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-6 and o.max_outer >= 2 and o.taper == 0
     assert o.graph == 1 and o.kernel == lsm.LSM_KERNEL_DIFF
+    assert o.residual == lsm.LSM_RESIDUAL_FP64   # the benchmark spec's FP64 refinement residual
 
 
 @pytest.mark.parametrize("n,ok", [((2, 2, 2), True), ((1, 4, 4), False), ((7, 4, 4), False),

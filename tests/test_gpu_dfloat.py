@@ -28,7 +28,7 @@ W = 2 * np.pi * 10.0
 @pytest.mark.parametrize("n", [(20, 18, 15), (12, 10, 8), (128, 6, 5), (5, 128, 6), (6, 5, 128), (128, 9, 128)])
 def test_apply_df_parity(n):
     med = sy.random_medium(n, h=8.0, seed=sum(n) + 1, frac=0.2)
-    h = handle(med, W, precision=lsm.LSM_MIXED)
+    h = handle(med, W, precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_DFLOAT)
     u = field(med.shape, 11)
     Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
     lsm.lsm_apply_df(h, dev(u).reshape(-1), Au)
@@ -41,7 +41,7 @@ def test_apply_df_parity(n):
 
 def test_apply_df_green_paper_and_taper():
     med = sy.random_medium((16, 12, 10), h=8.0, seed=71, frac=0.2)
-    h = handle(med, W, precision=lsm.LSM_MIXED, green=lsm.LSM_GREEN_PAPER, taper=3)
+    h = handle(med, W, precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_DFLOAT, green=lsm.LSM_GREEN_PAPER, taper=3)
     u = field(med.shape, 12)
     Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
     lsm.lsm_apply_df(h, dev(u).reshape(-1), Au)
@@ -54,7 +54,7 @@ def test_apply_df_green_paper_and_taper():
 def test_apply_df_hform_parity(n, mode, green):
     """The sampled-H form (Eq. 21 with the analytic H) in double-float arithmetic."""
     med = sy.random_medium(n, h=8.0, seed=sum(n) + 5, frac=0.2)
-    h = handle(med, W, precision=lsm.LSM_MIXED, green=green, kernel=lsm.LSM_KERNEL_H)
+    h = handle(med, W, precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_DFLOAT, green=green, kernel=lsm.LSM_KERNEL_H)
     u = field(med.shape, 14)
     Au = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
     lsm.lsm_apply_df(h, dev(u).reshape(-1), Au)
@@ -69,7 +69,7 @@ def test_mixed_solve_hform_pair_residual():
     oracle's solution of the same form."""
     med = sy.random_medium((12, 10, 9), h=10.0, seed=75, frac=0.1)
     w = 2 * np.pi * 9.0
-    h = handle(med, w, precision=lsm.LSM_MIXED, tol=1e-8, kernel=lsm.LSM_KERNEL_H)
+    h = handle(med, w, precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_DFLOAT, tol=1e-8, kernel=lsm.LSM_KERNEL_H)
     srcs = [(sy.explosion(), np.array([44.0, 41.0, 37.0])), (sy.double_couple_12(), np.array([31.0, 52.0, 45.0]))]
     bs, xs_, want = [], [], []
     F = op.FFTOperator(med, w, form="h")
@@ -130,7 +130,7 @@ def test_mixed_solve_pair_residual_nonzero_guess():
     """A nonzero initial iterate enters the first pair apply scaled by its own norm."""
     med = sy.random_medium((10, 9, 8), h=10.0, seed=74, frac=0.15)
     w = 2 * np.pi * 7.0
-    h = handle(med, w, precision=lsm.LSM_MIXED, tol=1e-9)
+    h = handle(med, w, precision=lsm.LSM_MIXED, residual=lsm.LSM_RESIDUAL_DFLOAT, tol=1e-9)
     b = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
     lsm.lsm_source(h, sy.explosion(), [41.0, 33.0, 29.0], b)
     x = b.clone() * 1e-3
