@@ -610,13 +610,14 @@ def main():
         copy_stream = torch.cuda.Stream()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         lsm.lsm_timer_start(R.base, False)
-        # one untimed copy into every pinned buffer: the first transfers into freshly pinned pages
+        # two untimed copies into every pinned buffer: the first transfers into freshly pinned pages
         # measured slow while kernels ran beside them
-        with torch.cuda.stream(copy_stream):
-            for k in range(2):
-                for j in range(R.wave):
-                    host[k][j].copy_(xsets[k][j], non_blocking=True)
-        copy_stream.synchronize()
+        for _ in range(2):
+            with torch.cuda.stream(copy_stream):
+                for k in range(2):
+                    for j in range(R.wave):
+                        host[k][j].copy_(xsets[k][j], non_blocking=True)
+            copy_stream.synchronize()
         # one untimed step: the solver's iteration graph is captured per stage-timer state
         R.step(timed_seq[0], xsets[1])
         lsm.lsm_timer_start(R.base, False)   # same timer state; zeroes the apply counters
