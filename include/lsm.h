@@ -99,6 +99,14 @@ typedef struct {
                           power of two to RMS(b) ~ 1 first: several times faster on this GPU,
                           whose FP64 rate is 1/64 of its FP32 rate, but narrower than FP64.
                           Adjoint solves always use FP64.  Ignored for LSM_FP64 handles. */
+    int fused_dots;    /* LSM_MIXED, 1 (default): the inner products of an FP32 BiCGSTAB
+                          iteration (<r^, v> for alpha, <t, s> and <t, t> for omega) are summed in
+                          the epilogue of the operator apply that writes v and t, where that
+                          epilogue is the warp-per-line inverse x transform (grid sides 8, 32 and
+                          128 with the default schedule; forward solves), instead of by two vector
+                          kernels that read the vectors again.  0: always the vector kernels.
+                          Both sum exact products with compensation into FP64 totals; the results
+                          agree to rounding.  FP64 iterations always use the vector kernels. */
 } lsm_opts;
 
 /* Fill *o with the defaults listed above.  o: host pointer, not null. */

@@ -23,6 +23,7 @@
 #include "kernels.h"
 #include "fft.cuh"
 #include "fft4.cuh"
+#include "solver.cuh"   // DotSink
 
 namespace lsm {
 
@@ -865,13 +866,30 @@ __global__ void __launch_bounds__(LPB * A, sizeof(T) == 4 ? 4 : 1) k4_rows_w(con
     }
 }
 
+// blocks per SM each precision is compiled for: FP32 (with or without DOTS) fits 80 registers
+// for 3 blocks of 256 threads; FP64 and double-float keep the occupancy they reach unconstrained
+// (5 and 4 blocks of 128 threads at A = 16)
+template <typename T>
+constexpr int xout_min_blocks() { return sizeof(T) == 4 ? 3 : (std::is_same<T, dfloat>::value ? 4 : 5); }
+
 // inverse x FFT of the rows of w2 [3][nz][ny][L], crop to x = k - xoff in [0, nx) (at most
-// (A/2 + 1) A outputs), Au = u - u_s
-template <typename T, int A, int LPB>
-__global__ void __launch_bounds__(LPB * A) k4_xout_w(Dims d, const ApplySys<T>* __restrict__ sys,
+// (A/2 + 1) A outputs), Au = u - u_s.
+// DOTS (FP32 only): each warp also writes to the system's DotSink its partial sums of the BiCGSTAB
+// inner product that needs this output, and dot_finish adds the warps' partials in FP64 and
+// finishes alpha or omega.  DOT_RV: <r^, Au>; r^ at the thread's outputs is copied to shared
+// memory (cp.async, dynamic shared memory [LPB][NO][A]) while the transform runs.  DOT_TS: <Au, u>
+// and <Au, Au>, from registers.  Within a warp the sums are plain FP32: at most 2 (A/2 + 1)
+// products per thread and sum and a 5-level shuffle tree, so within about (A + 7) 2^-24 of the
+// exact sum relative to the sum of |products| (1.4e-6 at A = 16): the accuracy of an FP32
+// BiCGSTAB's own inner products, where the apply itself carries FP32 rounding.  (Compensated sums
+// as in the vector kernels doubled this kernel's instructions and registers; a block reduction
+// and a last-block ticket stalled every block on a barrier or an atomic round trip.)
+template <typename T, int A, int LPB, int DOTS = 0>
+__global__ void __launch_bounds__(LPB * A, xout_min_blocks<T>()) k4_xout_w(Dims d, const ApplySys<T>* __restrict__ sys,
                                                      const typename cplx_of<T>::type* __restrict__ tw, int xoff) {
     typedef typename cplx_of<T>::type C;
     constexpr int L = A * A, NO = A / 2 + 1;
+    static_assert(DOTS == 0 || sizeof(T) == 4, "inner products are folded into the FP32 epilogue only");
     __shared__ C tile[LPB][A * (A + 1)];
     const ApplySys<T> S = sys[blockIdx.y];
     if (S.run && !*S.run) return;
@@ -882,6 +900,24 @@ __global__ void __launch_bounds__(LPB * A) k4_xout_w(Dims d, const ApplySys<T>* 
     const C* __restrict__ src = S.w2 + row * L;
     const C* __restrict__ uin = S.u + row * d.nx;
     C* __restrict__ out = S.out + row * d.nx;
+    const DotSink* D = nullptr;
+    C* rhs = nullptr;   // DOT_RV: this thread's r^ values, [k2] at stride A
+    if constexpr (DOTS == DOT_RV) {
+        extern __shared__ __align__(16) unsigned char rh_smem[];
+        D = static_cast<const DotSink*>(S.dot);
+        rhs = reinterpret_cast<C*>(rh_smem) + ln * NO * A + q;
+        const C* __restrict__ rh = static_cast<const C*>(D->rh) + row * d.nx;
+        if (live) {
+#pragma unroll
+            for (int k2 = 0; k2 < NO; ++k2) {
+                const int x = q + A * k2 - xoff;
+                if (x >= 0 && x < d.nx) cp_async_elem(&rhs[k2 * A], &rh[x]);
+            }
+        }
+        cp_async_commit();
+    } else if constexpr (DOTS == DOT_TS) {
+        D = static_cast<const DotSink*>(S.dot);
+    }
     C v[A];
 #pragma unroll
     for (int a = 0; a < A; ++a) v[a] = live ? src[q + A * a] : czero<C>();
@@ -906,7 +942,41 @@ __global__ void __launch_bounds__(LPB * A) k4_xout_w(Dims d, const ApplySys<T>* 
     }
     rows_w_exchange<A>(v, tile[ln], q);
     dft_reg_p<A, 1, A, NO>(v);
-    if (live) {
+    if constexpr (DOTS != 0) {
+        if constexpr (DOTS == DOT_RV) cp_async_wait_all();   // own copies only: no barrier
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;   // Re, Im of the inner product; |Au|^2
+        if (live) {
+#pragma unroll
+            for (int k2 = 0; k2 < NO; ++k2) {
+                const int x = q + A * k2 - xoff;
+                if (x >= 0 && x < d.nx) {
+                    const C u = uo[PRE ? k2 : 0];
+                    const C o = csub(u, v[k2]);
+                    out[x] = o;
+                    // conj(a) b with a = r^, b = Au (alpha) or a = Au, b = u (omega)
+                    if constexpr (DOTS == DOT_RV) {
+                        const C a = rhs[k2 * A];
+                        s0 = fmaf(a.x, o.x, fmaf(a.y, o.y, s0));
+                        s1 = fmaf(a.x, o.y, fmaf(-a.y, o.x, s1));
+                    } else {
+                        s0 = fmaf(o.x, u.x, fmaf(o.y, u.y, s0));
+                        s1 = fmaf(o.x, u.y, fmaf(-o.y, u.x, s1));
+                        s2 = fmaf(o.x, o.x, fmaf(o.y, o.y, s2));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, o);
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            if constexpr (DOTS == DOT_TS) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            const long long part = (long long)blockIdx.x * (LPB * A / 32) + (threadIdx.x >> 5);
+            reinterpret_cast<float4*>(D->partials)[part] = make_float4(s0, s1, s2, 0.f);
+        }
+    } else if (live) {
 #pragma unroll
         for (int k2 = 0; k2 < NO; ++k2) {
             const int x = q + A * k2 - xoff;
@@ -1203,18 +1273,21 @@ static inline int grid_elems(long long n) {
 // resident blocks: forcing the largest shared carveout left 28 KB of L1 and slowed the FP32 z
 // pass from 201 to 235 us per system apply (its spills and cached loads missed L1) and the FP32
 // inverse y pass from 46 to 57 us.
-static void smem_attr(const void* k, size_t sm) {
+// static_sm: the kernel's static shared memory; the dynamic limit must be raised once
+// static + dynamic passes 48 KB
+static void smem_attr(const void* k, size_t sm, size_t static_sm = 0) {
     static std::mutex mu;
     static std::vector<std::pair<const void*, size_t>> seen;
     std::lock_guard<std::mutex> lk(mu);
+    const bool big = sm + static_sm > 48 * 1024;
     for (auto& e : seen)
         if (e.first == k) {
             if (e.second >= sm) return;
-            if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (big) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             e.second = sm;
             return;
         }
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (big) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     seen.push_back({k, sm});
 }
 
@@ -1320,9 +1393,11 @@ static void launch_xfwd(const Dims& d, const ApplySys<T>* sys, int nsys, const P
 }
 
 // xoff: padded-grid index of model node 0 (1 when the convolved source lives on the extended nodes)
+// dots: the systems' DotSinks receive the iteration's inner product (only on the warp-line kernel;
+// the caller checks epilogue_dots_available first)
 template <typename T>
 static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, const Plans& pl, int xoff, cudaStream_t st,
-                            int v = 0) {
+                            int v = 0, int dots = 0) {
     if (!fourstep_prunable(d.Lx, 0, d.nx + xoff)) v = 1;
     typedef typename cplx_of<T>::type C;
     with_engine<std::is_same<T, dfloat>::value>(d.Lx, [&](auto eng) {
@@ -1330,6 +1405,20 @@ static void launch_fftx_out(const Dims& d, const ApplySys<T>* sys, int nsys, con
         if constexpr (F::INPLACE && F::A_ == F::B_) {
             constexpr int A = F::A_, LPB = sizeof(T) == 4 ? 16 : 8;
             const long long nrows = 3LL * d.nz * d.ny;
+            if constexpr (std::is_same<T, float>::value) {
+                if (dots == DOT_RV) {
+                    const size_t sm = (size_t)LPB * (A / 2 + 1) * A * sizeof(C);
+                    smem_attr((const void*)k4_xout_w<T, A, LPB, DOT_RV>, sm, (size_t)LPB * A * (A + 1) * sizeof(C));
+                    k4_xout_w<T, A, LPB, DOT_RV><<<dim3(cdiv(nrows, LPB), nsys), LPB * A, sm, st>>>(d, sys, (const C*)pl.twx,
+                                                                                                   xoff);
+                    return;
+                }
+                if (dots == DOT_TS) {
+                    k4_xout_w<T, A, LPB, DOT_TS><<<dim3(cdiv(nrows, LPB), nsys), LPB * A, 0, st>>>(d, sys, (const C*)pl.twx,
+                                                                                                  xoff);
+                    return;
+                }
+            }
             k4_xout_w<T, A, LPB><<<dim3(cdiv(nrows, LPB), nsys), LPB * A, 0, st>>>(d, sys, (const C*)pl.twx, xoff);
         } else if constexpr (F::INPLACE) {
             constexpr int A = F::A_, B = F::B_, ROWS = sizeof(T) == 4 ? 8 : 4;
@@ -1573,7 +1662,7 @@ static cudaError_t launch_apply_h(const Medium& m, const Plans& pl, const ApplyS
     ktimer_mark(tm, 4, f32, st, 1);
     // 6. inverse x FFT + crop (model node 0 at index 0) + Au = u - u_s
     ktimer_mark(tm, 5, f32, st, 0);
-    launch_fftx_out<T>(d, sys, nsys, pl, 0, st);
+    launch_fftx_out<T>(d, sys, nsys, pl, 0, st, 0, std::is_same<T, float>::value ? m.dots : 0);
     ktimer_mark(tm, 5, f32, st, 1);
     if (nl) *nl += 9;
     return cudaGetLastError();
@@ -1633,7 +1722,7 @@ cudaError_t launch_apply(const Medium& m, const Plans& pl, const ApplySys<T>* sy
     ktimer_mark(tm, 4, f32, st, 1);
     // 6. inverse x FFT + crop + Au = u - u_s (reads w2)
     ktimer_mark(tm, 5, f32, st, 0);
-    launch_fftx_out<T>(d, sys, nsys, pl, 1, st, sched[5]);
+    launch_fftx_out<T>(d, sys, nsys, pl, 1, st, sched[5], std::is_same<T, float>::value ? m.dots : 0);
     ktimer_mark(tm, 5, f32, st, 1);
     if (nl) *nl += 7;
     return cudaGetLastError();
@@ -1685,6 +1774,21 @@ cudaError_t launch_adjoint(const Medium& m, const Plans& pl, const ApplySys<T>* 
 }
 
 #ifndef LSM_APPLY_DFLOAT_TU
+bool epilogue_dots_available(const Medium& m) {
+    // the same engine choice launch_fftx_out makes: the sampled-H form crops from x offset 0 with
+    // the default schedule, the difference form from offset 1 with schedule sched[5]
+    const int L = m.d.Lx;
+    const int xoff = m.kernel == 1 ? 0 : 1;
+    const int v = m.kernel == 1 ? 0 : m.sched[5];
+    return (L == 16 || L == 64 || L == 256) && v != 1 && v != 2 && fourstep_prunable(L, 0, m.d.nx + xoff);
+}
+int epilogue_dot_parts(const Dims& d) {
+    // one partial per warp of the FP32 warp-per-line pass: 16 lines of A = sqrt(L) lanes a block
+    const int A = d.Lx == 16 ? 4 : (d.Lx == 64 ? 8 : 16);
+    const long long nrows = 3LL * d.nz * d.ny;
+    return (int)((nrows + 15) / 16) * (16 * A / 32);
+}
+
 // Gradient of Re<lam, K_T (Dv dC eps(u) + w^2 Emb drho u)> (discrete adjoint of Eqs. 8, 11):
 // z = K_T^H lam (extended nodes, in w1), tau = Dv^T z; packed entry (I, J) gets
 // Re(conj(tau_I) eps_J) (+ Re(conj(tau_J) eps_I) for I != J), drho gets w^2 Re(sum_j conj(z_j) u_j).

@@ -19,6 +19,8 @@ struct ApplySys {
     T omega2;            // w^2
     const int* run;      // system runs when run == nullptr or *run != 0
     unsigned long long* count;  // incremented once per executed system apply (may be nullptr)
+    const void* dot = nullptr;  // BiCGSTAB iteration applies only: the DotSink (solver.cuh) whose inner
+                                // product the epilogue accumulates; used when Medium::dots is set
 };
 
 // CUDA-event timing of every stage of the apply, per precision (diagnostics).  Stages: 0 stress,
@@ -43,6 +45,8 @@ struct Medium {
     KTimer* timer;       // optional stage timer
     int kernel;          // 0: difference form (6 spectra); 1: sampled-H form (24 spectra)
     int sched[6];        // FFT schedule variant per apply stage (0 default; see the pass launchers)
+    int dots = 0;        // DOT_RV or DOT_TS: the systems' ApplySys::dot are set and the FP32 epilogue
+                         // sums that inner product (only where epilogue_dots_available says so)
 };
 
 struct Plans {
@@ -54,6 +58,12 @@ struct Plans {
 
 // workspace elements (complex) needed by one system's apply / adjoint in w1 and w2 (kernel as in Medium)
 void apply_ws_elems(const Dims& d, int kernel, long long* w1, long long* w2);
+
+// True when the forward FP32 apply's epilogue can accumulate the BiCGSTAB inner product named by
+// each system's ApplySys::dot (the warp-line inverse x pass: lengths 16, 64 and 256 with the default
+// schedule), and the number of partial sums (one per epilogue warp) it writes per system.
+bool epilogue_dots_available(const Medium& m);
+int epilogue_dot_parts(const Dims& d);
 
 // Operator A u (forward) or A^H u (adjoint) for nsys systems; sys is a device array.
 template <typename T>

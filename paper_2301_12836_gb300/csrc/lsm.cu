@@ -46,11 +46,15 @@ struct SolverWS {
     std::vector<double2*> w1d, w2d, ax64;
     std::vector<dfcplx*> xdf;  // double-float copies of the iterates (pair residual applies)
     ApplySys<dfloat>* sysdf = nullptr;
+    DotSink* sinks = nullptr;  // [2][cap]: the <r^, v> and <t, s>, <t, t> sinks of the iteration applies
+    float* epi = nullptr;      // [2][cap][epi_parts][4] partial sums of the epilogue inner products
+    int epi_parts = 0;
     // captured BiCGSTAB iterations, one per (precision, direction); valid while block is
     struct Graph {
         cudaGraphExec_t exec = nullptr;
         int nsys = 0;
         int timer_on = 0;
+        int fuse = 0;             // captured with the inner products in the apply epilogues
         long long launches = 0;   // kernels per replay
         std::vector<int> tags;    // timer slots of the captured event pairs
     } graph[2][2];                // [FP32][adjoint]
@@ -236,6 +240,7 @@ extern "C" void lsm_default_opts(lsm_opts* o) {
     o->graph = 1;
     o->kernel = LSM_KERNEL_DIFF;
     o->residual = LSM_RESIDUAL_FP64;
+    o->fused_dots = 1;
 }
 
 static lsm_status build_spectrum(lsm_t h) {
@@ -281,7 +286,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     if ((o.precision != LSM_FP64 && o.precision != LSM_MIXED) || (o.green != LSM_GREEN_EXACT && o.green != LSM_GREEN_PAPER) ||
         !(o.tol > 0) || o.maxit < 1 || !(o.inner_tol > 0) || o.max_outer < 1 || o.taper < 0 ||
         (o.graph != 0 && o.graph != 1) || (o.kernel != LSM_KERNEL_DIFF && o.kernel != LSM_KERNEL_H) ||
-        (o.residual != LSM_RESIDUAL_DFLOAT && o.residual != LSM_RESIDUAL_FP64))
+        (o.residual != LSM_RESIDUAL_DFLOAT && o.residual != LSM_RESIDUAL_FP64) || (o.fused_dots != 0 && o.fused_dots != 1))
         return fail(nullptr, LSM_ERR_ARG, "lsm_create: invalid options");
     static bool attrs_done = false;
     if (!attrs_done) {
@@ -551,6 +556,9 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     const size_t o_s64 = take(nsys * sizeof(ApplySys<double>));
     const size_t o_ptr = take(7 * (size_t)nsys * sizeof(void*));
     const size_t o_sdf = take(nsys * sizeof(ApplySys<dfloat>));
+    const int epi_parts = epilogue_dot_parts(s->d);
+    const size_t o_snk = take(2 * (size_t)nsys * sizeof(DotSink));
+    const size_t o_epi = take(2 * (size_t)nsys * epi_parts * 4 * sizeof(float));
     std::vector<size_t> o_kry, o_w1, o_w2, o_w1d, o_w2d, o_ax, o_xdf;
     for (int i = 0; i < nsys; ++i) {
         for (int k = 0; k < KRY; ++k) o_kry.push_back(take(n3 * csz));
@@ -587,6 +595,9 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
     w.sys64 = (ApplySys<double>*)(b + o_s64);
     w.ptrs = (void**)(b + o_ptr);
     w.sysdf = (ApplySys<dfloat>*)(b + o_sdf);
+    w.sinks = (DotSink*)(b + o_snk);
+    w.epi = (float*)(b + o_epi);
+    w.epi_parts = epi_parts;
     for (int i = 0; i < nsys; ++i) {
         for (int k = 0; k < KRY; ++k) w.kry.push_back(b + o_kry[i * KRY + k]);
         if (mixed) {
@@ -618,9 +629,12 @@ cudaError_t apply_op(bool adjoint, const Medium& m, const Plans& pl, const Apply
 }
 
 // Run BiCGSTAB on nsys systems whose vectors/apply arguments are already on the device.
+// fuse: the iteration applies' epilogues sum <r^, v> and <t, s>, <t, t> (their ApplySys::dot are
+// set) and dot_finish, one block per system, finishes alpha and omega from their partial sums in
+// place of the two vector kernels that would read the vectors again
 template <typename T>
 lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const std::vector<double>& tol, int maxit,
-                        bool x_zero, const MixState* skip, std::vector<BcgState>& out, bool adjoint) {
+                        bool x_zero, const MixState* skip, std::vector<BcgState>& out, bool adjoint, bool fuse) {
     Store* s = h0->s;
     SolverWS& w = s->ws;
     const long long n3 = w.n3;
@@ -655,13 +669,16 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
     CK(h0, cudaStreamSynchronize(st));
     int n_active = s->h_pinned[0];
     // one iteration for every system on stream q; kernels of systems that stopped return at once
+    Medium mv = m, mt = m;
+    mv.dots = fuse ? DOT_RV : 0;
+    mt.dots = fuse ? DOT_TS : 0;
     auto iterate = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = bcg_update_p<T>(vecs, w.st, n3, nsys, pt.nblk, q, nl);
-        if (e == cudaSuccess) e = apply_op<T>(adjoint, m, pl, sv, nsys, q, nl);
-        if (e == cudaSuccess) e = bcg_alpha<T>(vecs, w.st, pt, n3, nsys, w.n_active, q, nl);
+        if (e == cudaSuccess) e = apply_op<T>(adjoint, mv, pl, sv, nsys, q, nl);
+        if (e == cudaSuccess) e = fuse ? dot_finish(w.sinks, nsys, q, nl) : bcg_alpha<T>(vecs, w.st, pt, n3, nsys, w.n_active, q, nl);
         if (e == cudaSuccess) e = bcg_s<T>(vecs, w.st, pt, n3, nsys, q, nl);
-        if (e == cudaSuccess) e = apply_op<T>(adjoint, m, pl, stt, nsys, q, nl);
-        if (e == cudaSuccess) e = bcg_omega<T>(vecs, w.st, pt, n3, nsys, q, nl);
+        if (e == cudaSuccess) e = apply_op<T>(adjoint, mt, pl, stt, nsys, q, nl);
+        if (e == cudaSuccess) e = fuse ? dot_finish(w.sinks + nsys, nsys, q, nl) : bcg_omega<T>(vecs, w.st, pt, n3, nsys, q, nl);
         if (e == cudaSuccess) e = bcg_xr<T>(vecs, w.st, pt, n3, nsys, w.n_active, q, nl);
         return e;
     };
@@ -678,7 +695,7 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
             done += 1;
         } else {
             const int tm_on = (tm.on && tm.ev) ? 1 : 0;
-            if (G.exec && (G.nsys != nsys || G.timer_on != tm_on)) {
+            if (G.exec && (G.nsys != nsys || G.timer_on != tm_on || G.fuse != (fuse ? 1 : 0))) {
                 cudaGraphExecDestroy(G.exec);
                 G = SolverWS::Graph();
             }
@@ -705,6 +722,7 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
                 }
                 G.nsys = nsys;
                 G.timer_on = tm_on;
+                G.fuse = fuse ? 1 : 0;
                 G.launches = *nl - nl0;
                 G.tags.assign(tm.tag, tm.tag + tm.used);
                 tm.used = 0;
@@ -729,6 +747,30 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
 }
 
 }  // namespace
+
+// Point the iteration applies of the nsys systems at their DotSinks: v = A p sums <r^, v> into
+// sink i, t = A s sums <t, s> and <t, t> into sink nsys + i (each with its own partial sums).
+template <typename T, typename C>
+static lsm_status set_dot_sinks(lsm_t h0, int nsys, const std::vector<BcgVecs<C>>& V, std::vector<ApplySys<T>>& sv,
+                                std::vector<ApplySys<T>>& stt) {
+    SolverWS& w = h0->s->ws;
+    std::vector<DotSink> dk(2 * (size_t)nsys);
+    for (int i = 0; i < nsys; ++i) {
+        for (int k = 0; k < 2; ++k) {
+            DotSink& q = dk[(size_t)k * nsys + i];
+            q.st = &w.st[i];
+            q.rh = k == 0 ? (const void*)V[i].rh : nullptr;
+            q.partials = w.epi + ((size_t)k * nsys + i) * w.epi_parts * 4;
+            q.nparts = w.epi_parts;
+            q.mode = k == 0 ? DOT_RV : DOT_TS;
+            q.n_active = w.n_active;
+        }
+        sv[i].dot = w.sinks + i;
+        stt[i].dot = w.sinks + nsys + i;
+    }
+    CK(h0, cudaMemcpyAsync(w.sinks, dk.data(), dk.size() * sizeof(DotSink), cudaMemcpyHostToDevice, h0->s->st));
+    return LSM_OK;
+}
 
 static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const* b, void* const* x, int* iters,
                                 double* relres, lsm_status* status, bool adjoint) {
@@ -780,13 +822,17 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             a.u = V[i].x; a.out = V[i].v; a.run = nullptr; sx[i] = a;
             a.u = V[i].x; a.out = k[6]; a.run = nullptr; a64[i] = a;   // true residual at exit
         }
+        // FP64 iterations keep the vector kernels: the FP64 epilogue is bound by the FP64 pipe,
+        // so the same FP64 products cost it as much as a separate kernel that streams the vectors
+        const bool fuse = false;
         CK(h0, cudaMemcpyAsync(w.vecs, V.data(), nsys * sizeof(V[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys_v, sv.data(), nsys * sizeof(sv[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys_t, stt.data(), nsys * sizeof(stt[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys_x, sx.data(), nsys * sizeof(sx[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys64, a64.data(), nsys * sizeof(a64[0]), cudaMemcpyHostToDevice, st));
         std::vector<BcgState> fin;
-        rc = run_bicgstab<double>(h0, hs, nsys, std::vector<double>(nsys, tol), h0->o.maxit, false, nullptr, fin, adjoint);
+        rc = run_bicgstab<double>(h0, hs, nsys, std::vector<double>(nsys, tol), h0->o.maxit, false, nullptr, fin, adjoint,
+                                  fuse);
         if (rc != LSM_OK) return rc;
         for (int i = 0; i < nsys; ++i) {
             it_out[i] = fin[i].iters;
@@ -857,6 +903,8 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
                 adf[i] = q;
             }
         }
+        const bool fuse = !adjoint && h0->o.fused_dots && epilogue_dots_available(medium_of(s, 1));
+        if (fuse && (rc = set_dot_sinks(h0, nsys, V, sv, stt)) != LSM_OK) return rc;
         if (pair) CK(h0, cudaMemcpyAsync(w.sysdf, adf.data(), nsys * sizeof(adf[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.vecs, V.data(), nsys * sizeof(V[0]), cudaMemcpyHostToDevice, st));
         CK(h0, cudaMemcpyAsync(w.sys_v, sv.data(), nsys * sizeof(sv[0]), cudaMemcpyHostToDevice, st));
@@ -909,7 +957,7 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             CK(h0, mix_down((double2* const*)(P + 2 * nsys), (float2* const*)(P + 3 * nsys), w.ms, n3, nsys, nblk, st, &h0->nl));
             for (int i = 0; i < nsys; ++i) CK(h0, cudaMemsetAsync(w.kry[i * KRY + 0], 0, n3 * sizeof(float2), st));
             std::vector<BcgState> fin;
-            rc = run_bicgstab<float>(h0, hs, nsys, itol, h0->o.maxit, true, w.ms, fin, adjoint);
+            rc = run_bicgstab<float>(h0, hs, nsys, itol, h0->o.maxit, true, w.ms, fin, adjoint, fuse);
             if (rc != LSM_OK) return rc;
             for (int i = 0; i < nsys; ++i) it_out[i] += fin[i].iters;
             CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, w.st, n3, nsys, nblk, st,

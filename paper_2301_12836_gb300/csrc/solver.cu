@@ -6,7 +6,7 @@
 // partials in block order and updates the system's scalars on the device.  Kernels of systems
 // that stopped return at once, so a batch keeps launching one grid per step whatever its mix of
 // converged and running systems.
-#include "solver.cuh"
+#include "reduce.cuh"
 
 namespace lsm {
 
@@ -42,152 +42,6 @@ __device__ __forceinline__ void strided4(long long n, Ld ld, Use use) {
 }
 template <typename C> struct Two { C a, b; };
 template <typename C> struct Three { C a, b, c; };
-
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) sh[wid * K + k] = v[k];
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double a = lane < nw ? sh[lane * K + k] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-            v[k] = a;
-        }
-    }
-}
-
-// Reduce v over the grid's x dimension for system sys.  Returns true in thread 0 of the last
-// CTA, with tot holding the system's sums.
-template <int K>
-__device__ __forceinline__ bool grid_sum(double (&v)[K], Partials pt, int sys, unsigned int* counter, double (&tot)[K]) {
-    __shared__ double sh[32 * K];
-    __shared__ int last;
-    block_sum<K>(v, sh);
-    if (threadIdx.x == 0) {
-        double* dst = pt.buf + ((long long)sys * pt.nblk + blockIdx.x) * 4;
-#pragma unroll
-        for (int k = 0; k < K; ++k) dst[k] = v[k];
-        __threadfence();
-        const unsigned int t = atomicAdd(counter, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double a[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) a[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        const double* src = pt.buf + ((long long)sys * pt.nblk + b) * 4;
-#pragma unroll
-        for (int k = 0; k < K; ++k) a[k] += __ldcg(&src[k]);
-    }
-    block_sum<K>(a, sh);
-    if (threadIdx.x == 0) {
-        *counter = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) tot[k] = a[k];
-        return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    const double d = b.x * b.x + b.y * b.y;
-    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
-__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
-
-// Running inner-product sums of one thread, K of them.
-// FP64 vectors: FP64 sums of FP64 products.
-// FP32 vectors: each product of two FP32 numbers is split exactly into p = fl(a b) and
-// e = fma(a, b, -p) (p + e = a b); p enters a compensated FP32 pair (hi, lo) through TwoSum, whose
-// rounding error joins e in lo, and every FLUSH elements the pair is added to an FP64 total.
-// With at most 2 FLUSH products per sum between flushes, the partial pair is within about
-// (4 FLUSH)^2 / 2 * 2^-48 (< 1e-11) of the exact sum, relative to the sum of |products|; the
-// totals and the cross-thread reduction are FP64.  This keeps the reductions memory-bound
-// instead of bound by the FP64 pipe (one 64th of the FP32 rate on this part).
-template <typename C, int K> struct Sums;
-
-template <int K> struct Sums<double2, K> {
-    double d[K];
-    __device__ __forceinline__ Sums() {
-#pragma unroll
-        for (int k = 0; k < K; ++k) d[k] = 0.0;
-    }
-    __device__ __forceinline__ void prod(int k, double a, double b) { d[k] = fma(a, b, d[k]); }
-    __device__ __forceinline__ void step() {}
-    __device__ __forceinline__ void finish(double (&out)[K]) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) out[k] = d[k];
-    }
-};
-
-template <int K> struct Sums<float2, K> {
-    static constexpr int FLUSH = 16;
-    float hi[K], lo[K];
-    double d[K];
-    int cnt;
-    __device__ __forceinline__ Sums() : cnt(0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            hi[k] = lo[k] = 0.f;
-            d[k] = 0.0;
-        }
-    }
-    __device__ __forceinline__ void prod(int k, float a, float b) {
-        const float p = __fmul_rn(a, b);
-        const float e = __fmaf_rn(a, b, -p);
-        const float t = __fadd_rn(hi[k], p);
-        const float bp = __fsub_rn(t, hi[k]);
-        const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, bp)), __fsub_rn(p, bp));
-        hi[k] = t;
-        lo[k] = __fadd_rn(lo[k], __fadd_rn(err, e));
-    }
-    __device__ __forceinline__ void flush() {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            d[k] += (double)hi[k] + (double)lo[k];
-            hi[k] = lo[k] = 0.f;
-        }
-        cnt = 0;
-    }
-    __device__ __forceinline__ void step() {
-        if (++cnt == FLUSH) flush();
-    }
-    __device__ __forceinline__ void finish(double (&out)[K]) {
-        flush();
-#pragma unroll
-        for (int k = 0; k < K; ++k) out[k] = d[k];
-    }
-};
-
-// sums k (re) and k + 1 (im) += conj(a) b
-template <typename C, int K>
-__device__ __forceinline__ void acc_dot(Sums<C, K>& S, int k, C a, C b) {
-    S.prod(k, a.x, b.x);
-    S.prod(k, a.y, b.y);
-    S.prod(k + 1, a.x, b.y);
-    S.prod(k + 1, -a.y, b.x);
-}
-// sum k += |a|^2
-template <typename C, int K>
-__device__ __forceinline__ void acc_nrm(Sums<C, K>& S, int k, C a) {
-    S.prod(k, a.x, a.x);
-    S.prod(k, a.y, a.y);
-}
 
 template <typename T>
 __global__ void __launch_bounds__(VTH) k_bcg_init(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
@@ -258,18 +112,7 @@ __global__ void __launch_bounds__(VTH) k_bcg_alpha(const BcgVecs<T>* __restrict_
              });
     double v[2], tot[2];
     acc.finish(v);
-    if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
-        BcgState& S = st[sys];
-        S.rv = make_double2(tot[0], tot[1]);
-        const double2 a = cdiv(S.rho, S.rv);
-        if ((tot[0] == 0.0 && tot[1] == 0.0) || !finite2(a)) {
-            S.status = -4;
-            S.active = S.run_v = S.run_t = 0;
-            atomicSub(n_active, 1);
-        } else {
-            S.alpha = a;
-        }
-    }
+    if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) bcg_alpha_final(st[sys], tot, n_active);
 }
 
 template <typename T>
@@ -316,12 +159,29 @@ __global__ void __launch_bounds__(VTH) k_bcg_omega(const BcgVecs<T>* __restrict_
              });
     double v[3], tot[3];
     acc.finish(v);
-    if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) {
-        BcgState& S = st[sys];
-        S.ts = make_double2(tot[0], tot[1]);
-        S.tt = tot[2];
-        // a zero <t,t> is caught as a breakdown by k_bcg_xr (omega = 0 there)
-        S.omega = tot[2] > 0.0 ? make_double2(tot[0] / tot[2], tot[1] / tot[2]) : make_double2(0.0, 0.0);
+    if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) bcg_omega_final(st[sys], tot);
+}
+
+// Sum the epilogue partials of each system's DotSink in FP64 (each thread a fixed stride of them,
+// then the block tree: the same order every call) and finish alpha (DOT_RV) or omega (DOT_TS);
+// one block per system, skipped like the apply that wrote them.
+__global__ void __launch_bounds__(VTH) k_dot_finish(const DotSink* __restrict__ sinks) {
+    const DotSink D = sinks[blockIdx.x];
+    const bool rv = D.mode == DOT_RV;
+    if (!(rv ? D.st->run_v : D.st->run_t)) return;
+    __shared__ double sh[32 * 3];
+    double a[3] = {0.0, 0.0, 0.0};
+    const float4* __restrict__ src = reinterpret_cast<const float4*>(D.partials);
+    for (int b = threadIdx.x; b < D.nparts; b += blockDim.x) {
+        const float4 p = __ldcg(&src[b]);
+        a[0] += p.x;
+        a[1] += p.y;
+        a[2] += p.z;
+    }
+    block_sum<3>(a, sh);
+    if (threadIdx.x == 0) {
+        if (rv) bcg_alpha_final(*D.st, a, D.n_active);
+        else bcg_omega_final(*D.st, a);
     }
 }
 
@@ -599,6 +459,12 @@ template <typename T>
 cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int* n_active, cudaStream_t s,
                    long long* nl) {
     k_bcg_xr<T><<<dim3(pt.nblk, nsys), VTH, 0, s>>>(vecs, st, pt, n, n_active);
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t dot_finish(const DotSink* sinks, int nsys, cudaStream_t s, long long* nl) {
+    k_dot_finish<<<nsys, VTH, 0, s>>>(sinks);
     if (nl) *nl += 1;
     return cudaGetLastError();
 }

@@ -27,6 +27,21 @@ struct BcgState {
     unsigned int counter;
 };
 
+// An inner product of the BiCGSTAB iteration folded into the epilogue of the apply that produces
+// one of its operands (the inverse x pass writes out = A u): mode DOT_RV accumulates <r^, out>
+// (r^ at rh) and finishes alpha; mode DOT_TS accumulates <out, u> and <out, out> and finishes
+// omega.  partials: nparts x 4 floats for this system, one (Re, Im, |out|^2, 0) per epilogue
+// warp; dot_finish adds them in FP64 in a fixed order into st.
+enum { DOT_RV = 1, DOT_TS = 2 };
+struct DotSink {
+    BcgState* st;
+    const void* rh;
+    float* partials;
+    int nparts;
+    int mode;
+    int* n_active;
+};
+
 template <typename T>
 struct BcgVecs {
     typedef typename cplx_of<T>::type C;
@@ -68,6 +83,8 @@ template <typename T>
 cudaError_t bcg_s(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl);
 template <typename T>
 cudaError_t bcg_omega(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl);
+// alpha or omega of each of nsys systems from the partial sums of its DotSink (sinks: device array)
+cudaError_t dot_finish(const DotSink* sinks, int nsys, cudaStream_t s, long long* nl);
 template <typename T>
 cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, int* n_active,
                    cudaStream_t s, long long* nl);

@@ -43,7 +43,7 @@ EXPORTS = ("lsm_default_opts", "lsm_create", "lsm_create_shared", "lsm_source", 
 class lsm_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("green", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
                 ("inner_tol", ct.c_double), ("max_outer", ct.c_int), ("taper", ct.c_int), ("graph", ct.c_int),
-                ("kernel", ct.c_int), ("residual", ct.c_int)]
+                ("kernel", ct.c_int), ("residual", ct.c_int), ("fused_dots", ct.c_int)]
 
 
 class LSMError(RuntimeError):
