@@ -452,10 +452,21 @@ class Runner:
         gc.collect()
 
 
-def stage_records(lsm, st_ms, st_launch, a64, a32, ms, n, kernel, pair, share):
+def fused_epilogue(n, precision, kernel, schedule):
+    """True when the FP32 inverse-x epilogue also sums the BiCGSTAB iteration's inner products
+    (lsm_opts.fused_dots, on by default): mixed solves on an x side of 8, 32 or 128 whose inverse-x
+    pass keeps its default schedule.  Then the applies v = A p (half the FP32 applies) also read
+    r^ (one more vector of 3 N complex64)."""
+    if precision != "mixed" or 2 * n[0] not in (16, 64, 256):
+        return False
+    v = 0 if (kernel == "h" or schedule is None) else schedule["fp32"][5]
+    return v not in (1, 2)
+
+
+def stage_records(lsm, st_ms, st_launch, a64, a32, ms, n, kernel, pair, share, fused=False):
     """Per-stage rooflines: FP32 stages against HBM (algorithmic bytes), FP64 stages against the
     FP64 pipe (model flops); double-float stages (FP32 pipe) against the HBM floor of their bytes
-    with their FP64-equivalent rate."""
+    with their FP64-equivalent rate.  fused: see fused_epilogue."""
     peak, _ = peaks()
     stages = []
     for slot in range(12):
@@ -472,6 +483,8 @@ def stage_records(lsm, st_ms, st_launch, a64, a32, ms, n, kernel, pair, share):
         sb, sf = (stage_bytes_h, stage_flops_h) if kernel == "h" else (stage_bytes, stage_flops)
         if f32:
             nbytes = sb(stage, n, 8, 4, share)
+            if stage == 5 and fused:
+                nbytes += 3 * n[0] * n[1] * n[2] * 8 / 2   # r^, read by half the applies
             ach = nbytes * napp / (st_ms[slot] / 1e3) / 1e9
             rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(ach / peak, 4), "algorithmic_bytes_per_system_apply": round(nbytes)})
@@ -580,7 +593,8 @@ def main():
     applies = a64 + a32
     ms_max, applies_all, solves_all, launches_all = reduce_timing(ms, applies, solves, launches, world, dist, "cuda")
     value = applies_all / (ms_max / 1e3)
-    stages = stage_records(lsm, st_ms, st_launch, a64, a32, ms, med.n, args.kernel, pair, nsys)
+    stages = stage_records(lsm, st_ms, st_launch, a64, a32, ms, med.n, args.kernel, pair, nsys,
+                           fused_epilogue(med.n, args.precision, args.kernel, schedule))
     dom = dict(stages[0]) if stages else {}
     if dom:
         prec_s = "mixed" if dom["kernel"].endswith("<float>") else ("dfloat" if dom["kernel"].endswith("<dfloat>") else "fp64")

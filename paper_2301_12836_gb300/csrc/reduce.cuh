@@ -78,7 +78,8 @@ __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isf
 // FP64 vectors: FP64 sums of FP64 products.
 // FP32 vectors: each product of two FP32 numbers is split exactly into p = fl(a b) and
 // e = fma(a, b, -p) (p + e = a b); p enters a compensated FP32 pair (hi, lo) through TwoSum, whose
-// rounding error joins e in lo, and every FLUSH elements the pair is added to an FP64 total.
+// rounding error joins e in lo, and after every FLUSH elements (strided4_sum calls flush() at
+// fixed points of its loop) the pair is added to an FP64 total.
 // With at most 2 FLUSH products per sum between flushes, the partial pair is within about
 // (4 FLUSH)^2 / 2 * 2^-48 (< 1e-11) of the exact sum, relative to the sum of |products|; the
 // totals and the cross-thread reduction are FP64.  This keeps the reductions memory-bound
@@ -91,8 +92,9 @@ template <int K> struct Sums<double2, K> {
 #pragma unroll
         for (int k = 0; k < K; ++k) d[k] = 0.0;
     }
+    static constexpr int FLUSH = 16;   // loop structure shared with the FP32 sums; nothing to flush
     __device__ __forceinline__ void prod(int k, double a, double b) { d[k] = fma(a, b, d[k]); }
-    __device__ __forceinline__ void step() {}
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ void finish(double (&out)[K]) {
 #pragma unroll
         for (int k = 0; k < K; ++k) out[k] = d[k];
@@ -111,8 +113,7 @@ template <int K> struct Sums<float2, K> {
     static constexpr int FLUSH = 16;
     float hi[K], lo[K];
     double d[K];
-    int cnt;
-    __device__ __forceinline__ Sums() : cnt(0) {
+    __device__ __forceinline__ Sums() {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             hi[k] = lo[k] = 0.f;
@@ -132,10 +133,6 @@ template <int K> struct Sums<float2, K> {
             d[k] += (double)hi[k] + (double)lo[k];
             hi[k] = lo[k] = 0.f;
         }
-        cnt = 0;
-    }
-    __device__ __forceinline__ void step() {
-        if (++cnt == FLUSH) flush();
     }
     __device__ __forceinline__ void finish(double (&out)[K]) {
         flush();

@@ -40,6 +40,42 @@ __device__ __forceinline__ void strided4(long long n, Ld ld, Use use) {
     }
     for (; i < n; i += S) use(i, ld(i));
 }
+// strided4 for the kernels that also sum: the elements go in the same order, and acc.flush()
+// (compensated FP32 pairs into FP64 totals) runs after every Acc::FLUSH elements of the main loop
+// as a fixed part of the loop.  (A counter test per element was if-converted by the compiler,
+// which then issued the FP64 flush for every element and bound these streams by the FP64 pipe.)
+template <class Acc, class Ld, class Use>
+__device__ __forceinline__ void strided4_sum(long long n, Acc& acc, Ld ld, Use use) {
+    constexpr int CH = Acc::FLUSH / 4;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (4LL * CH - 1) * S < n;) {
+#pragma unroll 1
+        for (int c = 0; c < CH; ++c, i += 4 * S) {
+            const auto v0 = ld(i);
+            const auto v1 = ld(i + S);
+            const auto v2 = ld(i + 2 * S);
+            const auto v3 = ld(i + 3 * S);
+            use(i, v0);
+            use(i + S, v1);
+            use(i + 2 * S, v2);
+            use(i + 3 * S, v3);
+        }
+        acc.flush();
+    }
+    // fewer than FLUSH elements remain: no flush before the caller's finish()
+    for (; i + 3 * S < n; i += 4 * S) {
+        const auto v0 = ld(i);
+        const auto v1 = ld(i + S);
+        const auto v2 = ld(i + 2 * S);
+        const auto v3 = ld(i + 3 * S);
+        use(i, v0);
+        use(i + S, v1);
+        use(i + 2 * S, v2);
+        use(i + 3 * S, v3);
+    }
+    for (; i < n; i += S) use(i, ld(i));
+}
 template <typename C> struct Two { C a, b; };
 template <typename C> struct Three { C a, b, c; };
 
@@ -52,15 +88,14 @@ __global__ void __launch_bounds__(VTH) k_bcg_init(const BcgVecs<T>* __restrict__
     if (skip && skip[sys].done) return;
     const BcgVecs<T> V = vecs[sys];
     Sums<C, 2> acc;
-    strided4(n, [&](long long i) { return Two<C>{V.b[i], x_zero ? czero<C>() : V.v[i]}; },
-             [&](long long i, const Two<C>& w) {
-                 const C r = x_zero ? w.a : csub(w.a, w.b);
-                 V.r[i] = r;
-                 V.rh[i] = r;
-                 acc_nrm(acc, 0, w.a);
-                 acc_nrm(acc, 1, r);
-                 acc.step();
-             });
+    strided4_sum(n, acc, [&](long long i) { return Two<C>{V.b[i], x_zero ? czero<C>() : V.v[i]}; },
+                 [&](long long i, const Two<C>& w) {
+                     const C r = x_zero ? w.a : csub(w.a, w.b);
+                     V.r[i] = r;
+                     V.rh[i] = r;
+                     acc_nrm(acc, 0, w.a);
+                     acc_nrm(acc, 1, r);
+                 });
     double v[2], tot[2];
     acc.finish(v);
     if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) {
@@ -105,11 +140,10 @@ __global__ void __launch_bounds__(VTH) k_bcg_alpha(const BcgVecs<T>* __restrict_
     if (!st[sys].run_v) return;
     const BcgVecs<T> V = vecs[sys];
     Sums<C, 2> acc;
-    strided4(n, [&](long long i) { return Two<C>{V.rh[i], V.v[i]}; },
-             [&](long long, const Two<C>& w) {
-                 acc_dot(acc, 0, w.a, w.b);
-                 acc.step();
-             });
+    strided4_sum(n, acc, [&](long long i) { return Two<C>{V.rh[i], V.v[i]}; },
+                 [&](long long, const Two<C>& w) {
+                     acc_dot(acc, 0, w.a, w.b);
+                 });
     double v[2], tot[2];
     acc.finish(v);
     if (grid_sum<2>(v, pt, sys, &st[sys].counter, tot)) bcg_alpha_final(st[sys], tot, n_active);
@@ -124,13 +158,12 @@ __global__ void __launch_bounds__(VTH) k_bcg_s(const BcgVecs<T>* __restrict__ ve
     const BcgVecs<T> V = vecs[sys];
     const C al = from_d2<C>(st[sys].alpha);
     Sums<C, 1> acc;
-    strided4(n, [&](long long i) { return Two<C>{V.r[i], V.v[i]}; },
-             [&](long long i, const Two<C>& w) {
-                 const C s = csub(w.a, cmul(al, w.b));
-                 V.s[i] = s;
-                 acc_nrm(acc, 0, s);
-                 acc.step();
-             });
+    strided4_sum(n, acc, [&](long long i) { return Two<C>{V.r[i], V.v[i]}; },
+                 [&](long long i, const Two<C>& w) {
+                     const C s = csub(w.a, cmul(al, w.b));
+                     V.s[i] = s;
+                     acc_nrm(acc, 0, s);
+                 });
     double v[1], tot[1];
     acc.finish(v);
     if (grid_sum<1>(v, pt, sys, &st[sys].counter, tot)) {
@@ -151,12 +184,11 @@ __global__ void __launch_bounds__(VTH) k_bcg_omega(const BcgVecs<T>* __restrict_
     if (!st[sys].run_t) return;
     const BcgVecs<T> V = vecs[sys];
     Sums<C, 3> acc;
-    strided4(n, [&](long long i) { return Two<C>{V.t[i], V.s[i]}; },
-             [&](long long, const Two<C>& w) {
-                 acc_dot(acc, 0, w.a, w.b);
-                 acc_nrm(acc, 2, w.a);
-                 acc.step();
-             });
+    strided4_sum(n, acc, [&](long long i) { return Two<C>{V.t[i], V.s[i]}; },
+                 [&](long long, const Two<C>& w) {
+                     acc_dot(acc, 0, w.a, w.b);
+                     acc_nrm(acc, 2, w.a);
+                 });
     double v[3], tot[3];
     acc.finish(v);
     if (grid_sum<3>(v, pt, sys, &st[sys].counter, tot)) bcg_omega_final(st[sys], tot);
@@ -186,7 +218,7 @@ __global__ void __launch_bounds__(VTH) k_dot_finish(const DotSink* __restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
+__global__ void __launch_bounds__(VTH, sizeof(T) == 4 ? 3 : 2) k_bcg_xr(const BcgVecs<T>* __restrict__ vecs, BcgState* __restrict__ st,
                                                 Partials pt, long long n, int* n_active) {
     typedef typename cplx_of<T>::type C;
     const int sys = blockIdx.y;
@@ -201,15 +233,14 @@ __global__ void __launch_bounds__(VTH) k_bcg_xr(const BcgVecs<T>* __restrict__ v
                  [&](long long i, const Two<C>& w) { V.x[i] = cadd(w.a, cmul(al, w.b)); });
     } else {
         struct Five { C s, t, x, p, rh; };
-        strided4(n, [&](long long i) { return Five{V.s[i], V.t[i], V.x[i], V.p[i], V.rh[i]}; },
-                 [&](long long i, const Five& w) {
-                     V.x[i] = cadd(w.x, cadd(cmul(al, w.p), cmul(om, w.s)));
-                     const C r = csub(w.s, cmul(om, w.t));
-                     V.r[i] = r;
-                     acc_nrm(acc, 0, r);
-                     acc_dot(acc, 1, w.rh, r);
-                     acc.step();
-                 });
+        strided4_sum(n, acc, [&](long long i) { return Five{V.s[i], V.t[i], V.x[i], V.p[i], V.rh[i]}; },
+                     [&](long long i, const Five& w) {
+                         V.x[i] = cadd(w.x, cadd(cmul(al, w.p), cmul(om, w.s)));
+                         const C r = csub(w.s, cmul(om, w.t));
+                         V.r[i] = r;
+                         acc_nrm(acc, 0, r);
+                         acc_dot(acc, 1, w.rh, r);
+                     });
     }
     double v[3], tot[3];
     acc.finish(v);
@@ -392,11 +423,10 @@ __global__ void k_mix_stall(MixState* __restrict__ ms, const BcgState* __restric
 __global__ void __launch_bounds__(VTH) k_dot_c64(const float2* __restrict__ a, const float2* __restrict__ b, long long n,
                                                  double* __restrict__ partial) {
     Sums<float2, 2> acc;
-    strided4(n, [&](long long i) { return Two<float2>{a[i], b[i]}; },
-             [&](long long, const Two<float2>& w) {
-                 acc_dot(acc, 0, w.a, w.b);
-                 acc.step();
-             });
+    strided4_sum(n, acc, [&](long long i) { return Two<float2>{a[i], b[i]}; },
+                 [&](long long, const Two<float2>& w) {
+                     acc_dot(acc, 0, w.a, w.b);
+                 });
     double v[2];
     acc.finish(v);
     __shared__ double sh[32 * 2];

@@ -21,6 +21,19 @@ def test_stage_bytes_model_128():
     assert all(bench.stage_bytes(s, N128, 8, 4, share=8) == bench.stage_bytes(s, N128, 8, 4) for s in (0, 1, 2, 4, 5))
 
 
+def test_fused_epilogue_cases():
+    """The FP32 inverse-x epilogue sums the iteration's inner products (and its v = A p applies
+    read r^) for mixed solves on x sides 8, 32 and 128 with that pass's default schedule."""
+    sched = {"fp64": [0] * 6, "fp32": [0] * 6}
+    assert bench.fused_epilogue(N128, "mixed", "diff", sched)
+    assert bench.fused_epilogue((32, 20, 24), "mixed", "diff", None)
+    assert bench.fused_epilogue((8, 6, 10), "mixed", "h", {"fp64": [0] * 6, "fp32": [0, 0, 0, 0, 0, 1]})
+    assert not bench.fused_epilogue(N128, "fp64", "diff", sched)
+    assert not bench.fused_epilogue((96, 96, 96), "mixed", "diff", sched)
+    assert not bench.fused_epilogue((64, 64, 64), "mixed", "diff", sched)
+    assert not bench.fused_epilogue(N128, "mixed", "diff", {"fp64": [0] * 6, "fp32": [0, 0, 0, 0, 0, 2]})
+
+
 def test_waves_cover_every_frequency():
     blocks = bench.freq_blocks(32, 8)
     assert blocks == [list(range(8 * k, 8 * k + 8)) for k in range(4)]

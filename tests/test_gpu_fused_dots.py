@@ -3,9 +3,9 @@
 With fused_dots = 1 the apply that writes v = A p also sums <r^, v> and the one that writes
 t = A s sums <t, s> and <t, t> (van der Vorst's BiCGSTAB, the alpha and omega steps of the
 iteration used for Eq. 22) in the FP32 iterations of mixed solves, on grids whose x side doubles to
-16, 64 or 256.  These tests solve the
-same systems with the epilogue sums and with the separate vector kernels, check both against the
-oracle's BiCGSTAB, and check that the fused path is deterministic.
+16, 64 or 256.  These tests solve the same systems with the epilogue sums and with the separate
+vector kernels, check both against the oracle's BiCGSTAB, and check that the fused path is
+deterministic.
 """
 import numpy as np
 import pytest
