@@ -98,7 +98,9 @@ struct Store {
     ApplySys<double>* a64 = nullptr;
     ApplySys<float>* a32 = nullptr;
     int* flag = nullptr;
-    int* h_pinned = nullptr;   // pinned host ints for readbacks
+    void* h_map = nullptr;     // mapped pinned host buffer for readback() and its device alias
+    void* d_map = nullptr;
+    size_t map_bytes = 0;
     unsigned long long* counts = nullptr;  // device: executed system applies [FP64, FP32]
     double* grad_scratch = nullptr;        // moment-gradient partial sums
     KTimer timer;
@@ -182,7 +184,7 @@ void store_release(Store* s) {
         delete[] s->timer.ev;
         delete[] s->timer.tag;
     }
-    if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    if (s->h_map) cudaFreeHost(s->h_map);
     drop_graphs(s->ws);
     cudaFree(s->ws.block);
     if (s->cap_st) cudaStreamDestroy(s->cap_st);
@@ -224,6 +226,42 @@ Medium medium_of(Store* s, int prec32) {
     m.kernel = s->kernel;
     for (int k = 0; k < 6; ++k) m.sched[k] = s->sched[prec32 ? 1 : 0][k];
     return m;
+}
+
+// Mapped host memory for the values the host reads back while a solve runs (the source flag,
+// the count of active systems, the systems' BiCGSTAB and refinement states).  A one-block kernel
+// stores them there (publish) instead of a device-to-host cudaMemcpyAsync: such a copy waits in
+// the copy engine's queue behind any large copy the caller has in flight on another stream
+// (measured: 6.4 GB of solutions copied beside a solve stalled it for the copies' whole 33 ms
+// per wave instead of overlapping).
+cudaError_t map_reserve(Store* s, size_t bytes) {
+    if (bytes <= s->map_bytes) return cudaSuccess;
+    if (s->h_map) {
+        cudaError_t e = cudaFreeHost(s->h_map);
+        s->h_map = s->d_map = nullptr;
+        s->map_bytes = 0;
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaHostAlloc(&s->h_map, bytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        s->h_map = nullptr;
+        return e;
+    }
+    e = cudaHostGetDevicePointer(&s->d_map, s->h_map, 0);
+    if (e != cudaSuccess) return e;
+    s->map_bytes = bytes;
+    return cudaSuccess;
+}
+
+// Copy bytes (a multiple of 4) of device memory at dsrc to the host buffer hdst after the work
+// queued on st so far; synchronizes st.
+lsm_status readback(lsm_t h, const void* dsrc, void* hdst, size_t bytes, cudaStream_t st) {
+    Store* s = h->s;
+    CK(h, map_reserve(s, bytes));
+    CK(h, publish(dsrc, s->d_map, bytes, st, &h->nl));
+    CK(h, cudaStreamSynchronize(st));
+    memcpy(hdst, s->h_map, bytes);
+    return LSM_OK;
 }
 
 }  // namespace
@@ -371,7 +409,7 @@ extern "C" lsm_status lsm_create(lsm_t* out, const int n[3], double dx, double l
     CKB(cudaMalloc(&s->flag, sizeof(int)));
     CKB(cudaMalloc(&s->counts, 2 * sizeof(unsigned long long)));
     CKB(cudaMemsetAsync(s->counts, 0, 2 * sizeof(unsigned long long), s->st));
-    CKB(cudaMallocHost(&s->h_pinned, 16 * sizeof(int)));
+    CKB(map_reserve(s, 4096));
     rc = build_spectrum(h);
     if (rc != LSM_OK) return bail(rc);
 #undef CKB
@@ -430,9 +468,10 @@ static lsm_status source_fields(lsm_t h, const char* who, int nm, const double* 
     CK(h, cudaMemsetAsync(s->flag, 0, sizeof(int), s->st));
     CK(h, launch_source(s->d, s->lam, s->mu, s->rho, h->omega, s->green, nm, M, xs, (double2* const*)u0, s->flag, s->st,
                         &h->nl));
-    CK(h, cudaMemcpyAsync(s->h_pinned, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->st));
-    CK(h, cudaStreamSynchronize(s->st));
-    if (s->h_pinned[0]) {
+    int on_node = 0;
+    lsm_status rb = readback(h, s->flag, &on_node, sizeof(int), s->st);
+    if (rb != LSM_OK) return rb;
+    if (on_node) {
         h->err = std::string(who) + ": a grid node coincides with the source; u0 set to 0 there";
         return LSM_WARN_SOURCE_ON_NODE;
     }
@@ -581,6 +620,9 @@ lsm_status ensure_solver_ws(lsm_t h, int nsys) {
         return cuda_fail(h, e, "solver workspace");
     }
     char* b = (char*)w.block;
+    // readbacks of the systems' states go through the mapped buffer: size it for this batch now
+    const size_t state_bytes = sizeof(BcgState) > sizeof(MixState) ? sizeof(BcgState) : sizeof(MixState);
+    CK(h, map_reserve(s, (size_t)nsys * state_bytes + 256));
     w.cap = nsys;
     w.precision = s->precision;
     w.n3 = n3;
@@ -665,9 +707,9 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
         if (e != cudaSuccess) return cuda_fail(h0, e, "initial residual apply");
     }
     CK(h0, bcg_init<T>(vecs, w.st, pt, n3, nsys, x_zero ? 1 : 0, skip, w.n_active, st, nl));
-    CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(h0, cudaStreamSynchronize(st));
-    int n_active = s->h_pinned[0];
+    int n_active = 0;
+    lsm_status rb = readback(h0, w.n_active, &n_active, sizeof(int), st);
+    if (rb != LSM_OK) return rb;
     // one iteration for every system on stream q; kernels of systems that stopped return at once
     Medium mv = m, mt = m;
     mv.dots = fuse ? DOT_RV : 0;
@@ -735,15 +777,11 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
             }
             done += GRAPH_ITERS;
         }
-        CK(h0, cudaMemcpyAsync(s->h_pinned, w.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(h0, cudaStreamSynchronize(st));
+        if ((rb = readback(h0, w.n_active, &n_active, sizeof(int), st)) != LSM_OK) return rb;
         ktimer_flush(&tm);
-        n_active = s->h_pinned[0];
     }
     out.resize(nsys);
-    CK(h0, cudaMemcpyAsync(out.data(), w.st, nsys * sizeof(BcgState), cudaMemcpyDeviceToHost, st));
-    CK(h0, cudaStreamSynchronize(st));
-    return LSM_OK;
+    return readback(h0, w.st, out.data(), nsys * sizeof(BcgState), st);
 }
 
 }  // namespace
@@ -857,8 +895,7 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
         CK(h0, cudaMemcpyAsync(w.ms, ms.data(), nsys * sizeof(MixState), cudaMemcpyHostToDevice, st));
         CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms, pt,
                             n3, nsys, w.n_active, st, &h0->nl));
-        CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
-        CK(h0, cudaStreamSynchronize(st));
+        if ((rc = readback(h0, w.ms, ms.data(), nsys * sizeof(MixState), st)) != LSM_OK) return rc;
         for (int i = 0; i < nsys; ++i) rr_out[i] = ms[i].relres;
     } else {
         // mixed precision: outer residual in double-float (pair) or FP64 arithmetic, FP64 storage, and
@@ -942,8 +979,7 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             CK(h0, cudaMemsetAsync(w.n_active, 0, sizeof(int), st));
             CK(h0, mix_residual((const double2* const*)P, (const double2* const*)(P + nsys), (double2* const*)(P + 2 * nsys), w.ms,
                                 pt, n3, nsys, w.n_active, st, &h0->nl, pair));
-            CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
-            CK(h0, cudaStreamSynchronize(st));
+            if ((rc = readback(h0, w.ms, ms.data(), nsys * sizeof(MixState), st)) != LSM_OK) return rc;
             ktimer_flush(&s->timer);
             int n_act = 0;
             for (int i = 0; i < nsys; ++i) n_act += !ms[i].done;
@@ -963,8 +999,7 @@ static lsm_status solve_batched(int nsys, const lsm_t* hs_in, const void* const*
             CK(h0, mix_up((double2* const*)(P + 4 * nsys), (float2* const*)(P + 5 * nsys), w.ms, w.st, n3, nsys, nblk, st,
                           &h0->nl));
         }
-        CK(h0, cudaMemcpyAsync(ms.data(), w.ms, nsys * sizeof(MixState), cudaMemcpyDeviceToHost, st));
-        CK(h0, cudaStreamSynchronize(st));
+        if ((rc = readback(h0, w.ms, ms.data(), nsys * sizeof(MixState), st)) != LSM_OK) return rc;
         for (int i = 0; i < nsys; ++i) {
             rr_out[i] = ms[i].relres;
             stat[i] = (ms[i].done && !ms[i].stalled) ? LSM_OK : LSM_ERR_NOCONV;

@@ -493,6 +493,18 @@ cudaError_t bcg_xr(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long 
     return cudaGetLastError();
 }
 
+// dst: mapped host memory (its device alias); one block of word stores
+__global__ void __launch_bounds__(VTH) k_publish(const unsigned int* __restrict__ src, unsigned int* dst, int words) {
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t publish(const void* src, void* dst, size_t bytes, cudaStream_t s, long long* nl) {
+    k_publish<<<1, VTH, 0, s>>>(static_cast<const unsigned int*>(src), static_cast<unsigned int*>(dst),
+                                (int)(bytes / sizeof(unsigned int)));
+    if (nl) *nl += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t dot_finish(const DotSink* sinks, int nsys, cudaStream_t s, long long* nl) {
     k_dot_finish<<<nsys, VTH, 0, s>>>(sinks);
     if (nl) *nl += 1;

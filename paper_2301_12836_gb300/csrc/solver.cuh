@@ -83,6 +83,9 @@ template <typename T>
 cudaError_t bcg_s(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl);
 template <typename T>
 cudaError_t bcg_omega(const BcgVecs<T>* vecs, BcgState* st, Partials pt, long long n, int nsys, cudaStream_t s, long long* nl);
+// Copy bytes (a multiple of 4) from device memory src to dst, the device alias of mapped host
+// memory, with one block of stores on stream s.
+cudaError_t publish(const void* src, void* dst, size_t bytes, cudaStream_t s, long long* nl);
 // alpha or omega of each of nsys systems from the partial sums of its DotSink (sinks: device array)
 cudaError_t dot_finish(const DotSink* sinks, int nsys, cudaStream_t s, long long* nl);
 template <typename T>
