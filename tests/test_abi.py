@@ -50,6 +50,20 @@ def test_default_opts(lib):
     assert o.tol == 1e-10 and o.maxit >= 100 and o.inner_tol == 1e-6 and o.max_outer >= 2 and o.taper == 0
     assert o.graph == 1 and o.kernel == lsm.LSM_KERNEL_DIFF
     assert o.residual == lsm.LSM_RESIDUAL_FP64   # the benchmark spec's FP64 refinement residual
+    assert o.fused_dots == 1   # alpha's and omega's inner products summed in the FP32 epilogue
+
+
+def test_opts_binding_matches_the_header():
+    """The ctypes lsm_opts lists the header's fields in the header's order with matching C types
+    (int / double), so the struct the binding passes has the library's layout."""
+    from paper_2301_12836_gb300 import lsm
+    with open(HEADER) as f:
+        text = f.read()
+    body = text[text.index("typedef struct {", text.index("LSM_RESIDUAL_FP64")):text.index("} lsm_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    decl = re.findall(r"\b(int|double)\s+(\w+)\s*;", body)
+    ctypes_of = {"int": ct.c_int, "double": ct.c_double}
+    assert [(n, ctypes_of[t]) for t, n in decl] == list(lsm.lsm_opts._fields_)
 
 
 @pytest.mark.parametrize("n,ok", [((2, 2, 2), True), ((1, 4, 4), False), ((7, 4, 4), False),
@@ -92,7 +106,8 @@ def test_bad_options_rejected(lib):
     arr = (ct.c_int * 3)(4, 4, 4)
     fake = ct.c_void_p(16)
     for kw in (dict(precision=7), dict(green=3), dict(tol=0.0), dict(maxit=0), dict(inner_tol=-1.0), dict(max_outer=0),
-               dict(taper=-2), dict(graph=2), dict(kernel=2), dict(kernel=-1)):
+               dict(taper=-2), dict(graph=2), dict(kernel=2), dict(kernel=-1), dict(residual=2),
+               dict(fused_dots=2), dict(fused_dots=-1)):
         o = lsm.lsm_default_opts(**kw)
         code = lib.lsm_create(ct.byref(out), arr, 10.0, 1e9, 1e9, 2000.0, fake, fake, 1.0, ct.byref(o), None)
         assert code == lsm.LSM_ERR_ARG, kw
