@@ -756,6 +756,8 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
                 if (e == cudaSuccess) e = e2;
                 if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
                 if (g) cudaGraphDestroy(g);
+                // the launchers counted the captured kernels: that is the count of one replay
+                const long long captured = *nl - nl0;
                 *nl = nl0;
                 if (e != cudaSuccess) {
                     G = SolverWS::Graph();
@@ -765,7 +767,7 @@ lsm_status run_bicgstab(lsm_t h0, const std::vector<lsm_t>& hs, int nsys, const 
                 G.nsys = nsys;
                 G.timer_on = tm_on;
                 G.fuse = fuse ? 1 : 0;
-                G.launches = *nl - nl0;
+                G.launches = captured;
                 G.tags.assign(tm.tag, tm.tag + tm.used);
                 tm.used = 0;
             }

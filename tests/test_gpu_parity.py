@@ -239,7 +239,10 @@ def test_solve_batched_frequencies_and_sources(precision, tol, bar):
 def test_graph_replay_matches_eager_launches(precision, tol):
     """The BiCGSTAB iterations replayed from a captured CUDA graph give bitwise the iterates of
     host-launched kernels (same kernels, same order, deterministic reductions); the graph is
-    reused by a second solve, and the stage timer still sees every apply."""
+    reused by a second solve, and the stage timer still sees every apply.  The library's launch
+    count includes the replayed graphs' kernels: it stays close to the host-launched count (a
+    replay runs two iterations, so it may launch one more iteration's kernels per inner solve,
+    and it reads the host's control values back once per replay instead of once per iteration)."""
     med = sy.random_medium((12, 10, 9), h=10.0, seed=31, frac=0.1)
     srcs = [(sy.explosion(), np.array([44.0, 41.0, 37.0])), (sy.double_couple_12(), np.array([31.0, 52.0, 45.0])),
             (sy.double_couple_13(), np.array([61.0, 22.0, 45.0]))]
@@ -255,16 +258,19 @@ def test_graph_replay_matches_eager_launches(precision, tol):
         for rep in range(2):
             lsm.lsm_timer_start(h, True)
             xs = [torch.zeros_like(b) for b in bs]
+            n0 = lsm.lsm_launch_count(h)
             code, its, rrs, sts = lsm.lsm_solve_batched([h] * len(bs), bs, xs)
+            nk = lsm.lsm_launch_count(h) - n0
             assert code == lsm.LSM_OK and all(r <= tol for r in rrs)
             ms, launches, applies = lsm.lsm_timer_read(h)
-            runs.append((torch.stack(xs).cpu(), its, rrs, applies))
+            runs.append((torch.stack(xs).cpu(), its, rrs, applies, nk))
             assert sum(launches) > 0 and sum(ms) > 0
         assert torch.equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
         out[graph] = runs[0]
     assert torch.equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
     assert tuple(out[0][3]) == tuple(out[1][3])   # executed system applies per precision
+    assert out[0][4] > 0 and 0.8 * out[0][4] <= out[1][4] <= 1.25 * out[0][4] + 30
 
 
 def test_solve_zero_rhs_and_noconv():
