@@ -324,7 +324,7 @@ long long lsm_launch_count(lsm_t h);
  * one z-marching kernel (no stress round trip through memory); v[1] forward
  * x pass, v[2] forward y pass, v[4] inverse y pass, v[5] inverse x pass and
  * epilogue: 0 = compile-time two-step FFT where the line length allows it
- * (16..256), 1 = runtime mixed-radix Stockham engine, 2 = the same with half
+ * (16..512), 1 = runtime mixed-radix Stockham engine, 2 = the same with half
  * its tile; v[3] z pass with the Green multiply: 0..2 as above (0 is the
  * register-resident kernel in FP32), 3 = the shared-memory two-step kernel.
  * Every variant computes the same operator.  precision: LSM_FP64 (the FP64

@@ -9,7 +9,7 @@
 //   k(4)_fftz_green  forward FFT along z, u-hat_i = sum_j G-hat_ij q-hat_j, inverse FFT along z, crop
 //   k(4)_strided  inverse FFT along y, crop
 //   k(4)_fftx_out inverse FFT along x, crop, Au = u - u_s
-// Power-of-two line lengths 16..256 use the compile-time four-step FFT kernels (k4_*), any other
+// Power-of-two line lengths 16..512 use the compile-time four-step FFT kernels (k4_*), any other
 // length the runtime mixed-radix Stockham kernels.
 // Only three displacement-like components pass through the FFTs: the derivative of the
 // Green tensor in Eq. 8 is applied as the central difference D_k in real space, which is
@@ -1303,12 +1303,13 @@ static bool fourstep_prunable(int L, int in_end, int out_end) {
         case 64: A = 8; B = 8; break;
         case 128: A = 8; B = 16; break;
         case 256: A = 16; B = 16; break;
+        case 512: A = 16; B = 32; break;
         default: return true;   // generic engine
     }
     return in_end <= (A / 2 + 1) * B && out_end <= A * (B / 2 + 1);
 }
 
-// Call fn with the FFT engine for line length L: compile-time four-step for 16..256 unless the
+// Call fn with the FFT engine for line length L: compile-time four-step for 16..512 unless the
 // schedule variant v asks for the generic engine (v = 1, 2), else generic.
 // ONLY256 (the double-float operator): the compile-time engine for L = 256 only, every other length
 // generic, which keeps that translation unit's build short.
@@ -1328,6 +1329,7 @@ static void with_engine(int L, Fn&& fn, int v = 0) {
             case 64: fn(FourStepFFT<8, 8>()); break;
             case 128: fn(FourStepFFT<8, 16>()); break;
             case 256: fn(FourStepFFT<16, 16>()); break;
+            case 512: fn(FourStepFFT<16, 32>()); break;
             default: fn(GenericFFT()); break;
         }
     }

@@ -105,10 +105,61 @@ template <int S, int NZ, int NO, typename C> __device__ __forceinline__ void bfl
     b16_last<S, NO, 3>(y, v);
 }
 
+// W32^k a, W32^k = cos(2 pi k/32) + S i sin(2 pi k/32), k < 16 a compile-time constant after
+// unrolling
+template <int S, typename C> __device__ __forceinline__ C tw32(C a, int k) {
+    const double c1 = 0.98078528040323044913, s1 = 0.19509032201612826785;  // cos, sin(pi/16)
+    const double c2 = 0.92387953251128675613, s2 = 0.38268343236508977173;  // cos, sin(pi/8)
+    const double c3 = 0.83146961230254523708, s3 = 0.55557023301960222474;  // cos, sin(3 pi/16)
+    const double r2 = 0.70710678118654752440;
+    switch (k) {
+        case 0: return a;
+        case 1: return cmul_const<S>(a, c1, s1);
+        case 2: return cmul_const<S>(a, c2, s2);
+        case 3: return cmul_const<S>(a, c3, s3);
+        case 4: return cmul_const<S>(a, r2, r2);
+        case 5: return cmul_const<S>(a, s3, c3);
+        case 6: return cmul_const<S>(a, s2, c2);
+        case 7: return cmul_const<S>(a, s1, c1);
+        case 8: return cmul_si<S>(a);
+        case 9: return cmul_const<S>(a, -s1, c1);
+        case 10: return cmul_const<S>(a, -s2, c2);
+        case 11: return cmul_const<S>(a, -s3, c3);
+        case 12: return cmul_const<S>(a, -r2, r2);
+        case 13: return cmul_const<S>(a, -c3, s3);
+        case 14: return cmul_const<S>(a, -c2, s2);
+        default: return cmul_const<S>(a, -c1, s1);
+    }
+}
+
+// 32-point DFT in registers, natural order in and out, inputs NZ..31 zero and only the first NO
+// outputs wanted: radix 2 over the 16-point DFTs E of the even and O of the odd samples,
+// X[k] = E[k] + W32^k O[k] and X[k + 16] = E[k] - W32^k O[k] (k < 16).  The even samples keep
+// (NZ + 1) / 2 nonzero inputs, the odd ones NZ / 2, and both halves need outputs k < min(NO, 16).
+template <int S, int NZ, int NO, typename C> __device__ __forceinline__ void bfly32p(C* v) {
+    constexpr int NZE = (NZ + 1) / 2, NZO = NZ / 2, NH = NO < 16 ? NO : 16;
+    C e[16], o[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        e[j] = v[2 * j];
+        o[j] = v[2 * j + 1];
+    }
+    bfly16p<S, NZE, NH>(e);
+    if constexpr (NZO >= 1) bfly16p<S, NZO, NH>(o);
+#pragma unroll
+    for (int k = 0; k < NH; ++k) {
+        const C t = NZO >= 1 ? tw32<S>(o[k], k) : czero<C>();
+        v[k] = cadd(e[k], t);
+        if (k + 16 < NO) v[k + 16] = csub(e[k], t);
+    }
+}
+
 // R-point DFT with inputs NZ..R-1 zero and only the first NO outputs needed.  Pruned forms exist
-// for R = 16 and 4 (and R = 8 with NZ <= 4, R = 2 with NZ = 1); otherwise the full DFT runs.
+// for R = 32, 16 and 4 (and R = 8 with NZ <= 4, R = 2 with NZ = 1); otherwise the full DFT runs.
 template <int R, int S, int NZ, int NO, typename C> __device__ __forceinline__ void dft_reg_p(C* v) {
-    if constexpr (R == 16) {
+    if constexpr (R == 32) {
+        bfly32p<S, NZ, NO>(v);
+    } else if constexpr (R == 16) {
         bfly16p<S, NZ, NO>(v);
     } else if constexpr (R == 4) {
         bfly4p<S, NZ, NO>(v);
@@ -123,7 +174,9 @@ template <int R, int S, int NZ, int NO, typename C> __device__ __forceinline__ v
 
 // R-point DFT in registers; HALF: inputs R/2 .. R-1 are zero.
 template <int R, int S, bool HALF = false, typename C> __device__ __forceinline__ void dft_reg(C* v) {
-    if (R == 2) {
+    if constexpr (R == 32) {
+        bfly32p<S, HALF ? 16 : 32, 32>(v);
+    } else if (R == 2) {
         if (HALF) v[1] = v[0];
         else bfly2<S>(v);
     } else if (R == 4) {

@@ -1,10 +1,15 @@
-"""Parity with the oracle at the full-size FFT length (2n = 256), element by element.
+"""Parity with the oracle at the full-size FFT lengths (2n = 256, and 512 for the 256^3 workload),
+element by element.
 
 The kernels a 128^3 solve runs at L = 256 (the register-resident FP32 z pass, the FP64 z pass
 with its spectrum slice, the warp-line x rows and the strided y passes) are compiled for that
 length only, so small cubic grids never reach them.  Thin grids with a 128-node axis along x, y
 or z reach each of them at a cost the oracle finishes in a second or two; one full 128^3 apply
 of the benchmark's medium checks them all together.
+
+The 256-node axes of the 256^3 workload pad to L = 512, whose two-step kernels (16 x 32, with
+the 32-point DFT in registers) are compiled for that length only: thin grids with a 256-node
+axis reach them the same way.
 
 Tolerances as in test_gpu_parity: FP64 1e-12, FP32 1e-5 (relative L2).
 """
@@ -22,9 +27,10 @@ pytestmark = pytest.mark.gpu
 
 W = 2 * np.pi * 10.0
 THIN = [(128, 6, 5), (5, 128, 6), (6, 5, 128), (128, 9, 128)]
+THIN512 = [(256, 6, 5), (5, 256, 6), (6, 5, 256), (256, 5, 256)]
 
 
-@pytest.mark.parametrize("n", THIN)
+@pytest.mark.parametrize("n", THIN + THIN512)
 def test_apply_fp64_full_length(n):
     med = sy.random_medium(n, h=8.0, seed=sum(n) + 7, frac=0.2)
     h = handle(med, W)
@@ -36,7 +42,7 @@ def test_apply_fp64_full_length(n):
     assert rel(u, want) > 1e-3
 
 
-@pytest.mark.parametrize("n", THIN)
+@pytest.mark.parametrize("n", THIN + THIN512)
 def test_apply_fp32_full_length(n):
     med = sy.random_medium(n, h=8.0, seed=sum(n) + 8, frac=0.2)
     h = handle(med, W, precision=lsm.LSM_MIXED)
@@ -47,7 +53,7 @@ def test_apply_fp32_full_length(n):
     assert rel(host(Au).reshape(u.shape).astype(np.complex128), want) < 1e-5
 
 
-@pytest.mark.parametrize("n", [(6, 5, 128), (128, 9, 128)])
+@pytest.mark.parametrize("n", [(6, 5, 128), (128, 9, 128), (6, 5, 256), (256, 5, 256)])
 def test_adjoint_fp64_full_length(n):
     med = sy.random_medium(n, h=8.0, seed=sum(n) + 9, frac=0.2)
     h = handle(med, W)
@@ -73,3 +79,26 @@ def test_apply_full_128_cube_against_the_oracle():
     lsm.lsm_apply_c64(h, dev(u, torch.complex64).reshape(-1), A32)
     assert rel(host(A32).reshape(u.shape).astype(np.complex128), want) < 1e-5
     assert rel(u, want) > 1e-3
+
+
+@pytest.mark.parametrize("n", [(256, 6, 5), (6, 5, 256)])
+def test_hform_and_mixed_solve_at_length_512(n):
+    """The sampled-H form's plain transforms at L = 512 (FP64 apply against the oracle's H form),
+    and a mixed solve on the same grid against the oracle's BiCGSTAB."""
+    from oracle import solver as osv, source as osrc
+    med = sy.random_medium(n, h=8.0, seed=sum(n) + 10, frac=0.1)
+    hh = handle(med, W, kernel=lsm.LSM_KERNEL_H)
+    u = field(med.shape, 15)
+    Au = torch.empty(3 * hh.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_apply(hh, dev(u).reshape(-1), Au)
+    assert rel(host(Au).reshape(u.shape), op.FFTOperator(med, W, form="h").apply(u)) < 1e-12
+    h = handle(med, W, precision=lsm.LSM_MIXED, tol=1e-8)
+    xs = np.array(med.n, dtype=float) * med.h * 0.4
+    b = torch.empty(3 * h.N, dtype=torch.complex128, device="cuda")
+    lsm.lsm_source(h, sy.explosion(), xs, b)
+    x = torch.zeros_like(b)
+    code, it, rr = lsm.lsm_solve(h, b, x)
+    assert code == lsm.LSM_OK and rr <= 1e-8
+    u0, _ = osrc.background_field(med.n, med.h, sy.explosion(), xs, W, med.lam0, med.mu0, med.rho0)
+    xo, *_ = osv.bicgstab(op.FFTOperator(med, W).apply, u0, tol=1e-12, maxit=400)
+    assert rel(host(x).reshape(u0.shape), xo) < 1e-6
